@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark: Gcell-updates/s of the swept FP64 heat path on one GB300.
+
+Workload (one bench step): the FTCS heat equation, FP64, periodic grid of
+N = 2^24 cells, r drawn U[0.1, 0.45] (seeded), initial state a sum of 32 seeded
+sine modes, advanced 50,000 time steps by the swept rule (Up Triangle, Diamonds,
+Down Triangle; Section 3.1) with the tile base width chosen by a short timed
+sweep over W in {32, ..., 1024} (the paper's advice in Section 5: tune over a
+limited number of steps). One cell-update = one cell advanced one time step.
+
+Printed (rank 0, one JSON line): the swept value, the per-step ("Classic")
+kernel and the FP32 / FP32-compensated forms on the same grid with their errors
+against the FP64 oracle's closed form, a roofline entry for the dominant kernel
+(the Diamond phase) and the oracle timed on the host cores.
+
+``--impl reference`` times the FP64 CPU oracle itself (the only reference this
+paper has: no code was published with it) on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 1 << 24
+STEPS = 50_000
+MODES = 32
+SEED = 2024
+WIDTHS = (32, 64, 128, 256, 512, 1024)
+TUNE_STEPS = 4096
+METRIC = "Gcell-updates/s, swept vs per-step kernel, FP32/FP64 at stated err; % roofline"
+UNIT = "Gcell-updates/s"
+WORKLOAD = "heat FTCS FP64 periodic N=2^24, r~U[0.1,0.45] seed 2024, 32 sine modes, 50000 steps, swept"
+FLOPS_PER_UPDATE = 5  # a + b, fma(-2, u, .), fma(r, ., u): 1 add + 2 FMA
+# FP64 peak: 152 SMs x 2 FP64 FMA / clock / SM x 2 flop x 2.07 GHz (the GB300
+# part's 1.25 TFLOP/s dense FP64 at its maximum SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), \
+        int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def initial_state():
+    from paper_1811_08282_gb300 import inputs as I
+    modes = I.heat_modes(N, MODES, seed=SEED)
+    r = I.heat_r(SEED)
+    return modes, r, I.heat_initial(modes)
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1811_08282_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernels are unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        k, v = line.split("=", 1)
+        vals[k.strip()] = v.strip()
+    if vals.get("source_sha") != kernel_source_sha() or f"{kernel}.bytes_per_launch" not in vals:
+        return None
+    return float(vals[f"{kernel}.bytes_per_launch"])
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        self.path = None
+        self.uuid = uuid
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for rec in csv.reader(io.StringIO(open(self.path).read())):
+            if len(rec) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(rec[1]), smax=float(rec[2]), power=float(rec[3]),
+                                 hw=rec[5].strip(), hwt=rec[6].strip(), swt=rec[7].strip(), pcap=rec[8].strip()))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    from paper_1811_08282_gb300 import build
+    build.build()
+    from paper_1811_08282_gb300 import swept as S
+
+    modes, r, u0 = initial_state()
+    stream = torch.cuda.current_stream()
+    u0_dev = torch.as_tensor(u0, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def problem(prec, method, W):
+        return S.Problem(scheme=S.SW_HEAT, precision=prec, boundary=S.SW_PERIODIC, method=method, n=N, r=r,
+                         tile_width=W if method == S.SW_SWEPT else 0)
+
+    def timed_run(h, state, steps, reset_from=None):
+        if reset_from is not None:
+            state.copy_(reset_from)
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.sw_run(state, steps, stream)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    # 1) tile width: short timed sweep (Section 5: tune over a limited number of steps)
+    sweep = {}
+    for W in WIDTHS:
+        p = problem(S.SW_FP64, S.SW_SWEPT, W)
+        st = S.to_state(p, u0_dev)
+        with S.Handle(p) as h:
+            timed_run(h, st, 64, u0_dev)
+            t = timed_run(h, st, TUNE_STEPS, u0_dev)
+        sweep[W] = N * TUNE_STEPS / t / 1e9
+        del st
+    best_w = max(sweep, key=sweep.get)
+
+    # 2) warm-up and K timed steps of the full workload at the chosen width
+    p = problem(S.SW_FP64, S.SW_SWEPT, best_w)
+    state = S.to_state(p, u0_dev)
+    h = S.Handle(p)
+    for _ in range(args.warmup):
+        timed_run(h, state, STEPS, u0_dev)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    times = []
+    launches = 0
+    barrier()
+    sampler.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        if k == args.steps - 1:
+            h.sw_set_timing(STEPS // (best_w // 2) + 2)
+        times.append(timed_run(h, state, STEPS, u0_dev))
+        launches += h.sw_last_launch_count()
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    traced = h.sw_launch_times()
+    h.sw_set_timing(0)
+    final = S.to_fp64(p, state)[0]
+    t_total = sum(times)
+    if world > 1:
+        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = world * N * STEPS * args.steps / t_total / 1e9
+    ms_per_step = t_total / args.steps * 1e3
+
+    # roofline of the dominant kernel (Diamond phases), from the traced launches
+    diamonds = [ms for ms, kind in traced if kind == 1]
+    H = best_w // 2
+    flops_per_launch = N * H * FLOPS_PER_UPDATE
+    achieved = flops_per_launch / (statistics.mean(diamonds) / 1e3) / 1e12 if diamonds else None
+    traffic = recorded_traffic("k_swept_phase_heat_fp64")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": traffic,
+                "kernel": "k_swept_phase<HeatPolicy<FP64>> (Diamond)", "launches_traced": len(diamonds),
+                "avg_launch_ms": statistics.mean(diamonds) if diamonds else None,
+                "flops_per_launch": flops_per_launch,
+                "peak_source": "FP64 1.25 TFLOP/s class: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz (nominal, recipe)"}
+
+    # 3) end to end through the C ABI with host buffers (H2D + run + D2H inside the region)
+    host_in = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    host_in.copy_(torch.as_tensor(u0))
+    host_out = torch.empty_like(host_in)
+    e2e_times = []
+    for k in range(max(1, min(args.steps, 2)) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.sw_run_host(host_in.data_ptr(), host_out.data_ptr(), STEPS, stream)
+        t1 = time.perf_counter()
+        if k > 0:
+            e2e_times.append(t1 - t0)
+    e2e = {"value": N * STEPS / statistics.mean(e2e_times) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8,
+           "api": "sw_run_host (pinned host buffers)"}
+    h.close()
+
+    # 4) comparisons on the same grid: per-step kernel and the FP32 forms
+    compare = {}
+    outputs = {("fp64", "swept", STEPS): final.cpu()}
+    for name, prec in (("fp64", S.SW_FP64), ("fp32", S.SW_FP32), ("fp32_comp", S.SW_FP32_COMP)):
+        for method in ("swept", "perstep"):
+            if name == "fp64" and method == "swept":
+                compare["fp64_swept"] = {"value": value / world, "steps": STEPS, "W": best_w}
+                continue
+            steps = STEPS if method == "swept" else 5000
+            W = best_w if name == "fp64" else 1024
+            pp = problem(prec, S.SW_SWEPT if method == "swept" else S.SW_PERSTEP, W)
+            st = S.to_state(pp, u0_dev)
+            fresh = st.clone()
+            with S.Handle(pp) as hh:
+                timed_run(hh, st, min(steps, 256), fresh)  # warm-up
+                t = timed_run(hh, st, steps, fresh)
+            compare[f"{name}_{method}"] = {"value": N * steps / t / 1e9, "steps": steps,
+                                           "W": W if method == "swept" else None}
+            outputs[(name, method, steps)] = S.to_fp64(pp, st)[0].cpu()
+            del st, fresh
+    perstep_bytes = 16  # FP64 per-step: read + write one value per update
+    compare["fp64_perstep"]["hbm_gbs"] = compare["fp64_perstep"]["value"] * perstep_bytes
+    compare["speedup_swept_over_perstep_fp64"] = compare["fp64_swept"]["value"] / compare["fp64_perstep"]["value"]
+    compare["speedup_swept_over_perstep_fp32"] = compare["fp32_swept"]["value"] / compare["fp32_perstep"]["value"]
+    compare["speedup_swept_over_perstep_fp32_comp"] = (compare["fp32_comp_swept"]["value"]
+                                                        / compare["fp32_comp_perstep"]["value"])
+
+    # 5) CPU baseline (rank 0 only): the FP64 oracle on the host cores, bounded
+    #    sample; also states each result's error against the oracle's closed form.
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = cpu_baseline_leg(modes, r, u0, outputs, compare)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "time_steps": STEPS, "tile_width": best_w,
+                   "r": r, "modes": MODES, "parallelism": f"replicas x{world}",
+                   "l2": "flushed (256 MB write) before every timed step; state reset from a device copy"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks, "wall_s_timed_region": wall, "tile_sweep_gcups": sweep, "compare": compare,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline_leg(modes, r, u0, outputs, compare):
+    import numpy as np
+
+    import oracle
+    # error of every GPU result against the closed form (sampled cells)
+    idx = np.linspace(0, N - 1, 4096).astype(np.int64)
+    for (name, method, steps), out in outputs.items():
+        want = oracle.heat_modes(N, r, steps, modes.amps, modes.ks, idx)
+        got = out.numpy()[idx]
+        err = float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
+        compare.setdefault(f"{name}_{method}", {})["err_vs_oracle"] = err
+    # timing: oracle FTCS stepping on the full grid, a bounded number of steps
+    t0 = time.perf_counter()
+    oracle.heat_run(u0, r, 2)
+    per_step = (time.perf_counter() - t0) / 2
+    steps = max(2, min(200, int(15.0 / max(per_step, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.heat_run(u0, r, steps)
+    t = time.perf_counter() - t0
+    return {"value": N * steps / t / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"N=2^24, first {steps} of {STEPS} steps (naive FP64 stepping, OpenMP over cells)",
+            "cpu": _cpu_model()}
+
+
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    modes, r, u0 = initial_state()
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.heat_run(u0, r, 1)
+    per_step = time.perf_counter() - t0
+    # each bench step: a bounded sample of the workload (~5 s of CPU work)
+    steps = max(1, min(100, int(5.0 / max(per_step, 1e-6))))
+    for _ in range(args.warmup):
+        oracle.heat_run(u0, r, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.heat_run(u0, r, steps)
+        times.append(time.perf_counter() - t0)
+    t = sum(times)
+    value = N * steps * args.steps / t / 1e9
+    cpu = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"N=2^24, {steps} of {STEPS} steps per bench step (naive FP64 stepping)",
+           "cpu": _cpu_model()}
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n": N, "time_steps": STEPS},
+        "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                     "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

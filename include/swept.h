@@ -1,0 +1,168 @@
+/*
+ * swept.h -- C ABI of libswept.so: the swept time-space decomposition rule for
+ * explicit 1D stencils on one GB300 GPU (sm_103a), beside a per-time-step kernel.
+ *
+ * Paper: Magee, Walker & Niemeyer, "Applying the swept rule for solving explicit
+ * partial differential equations on heterogeneous computing systems".
+ *   Section 3.1 / Fig. 1:  Up Triangle, Communication, Diamond, Down Triangle.
+ *   Section 3.2:           the problem statement (grid size, block size, scheme)
+ *                          and the two test equations.
+ *   Section 3.3 / Fig. 2:  per-step ("Classic") decomposition, flattening and
+ *                          lengthening; the 7-value Euler state per point.
+ *
+ * Conventions for every entry point:
+ *  - All calls return an int status: 0 (SW_OK), a positive warning, or a
+ *    negative error (SW_ERR_*). No call throws or aborts across the ABI.
+ *  - Device pointers are CUDA global-memory pointers on the current device.
+ *    `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Compute calls are asynchronous on that stream; errors detected on the
+ *    device are latched in the handle and reported by sw_sync_status.
+ *  - The caller owns every state buffer it passes; the library owns the
+ *    scratch it allocates in sw_create and frees it in sw_destroy.
+ *  - A handle is not thread-safe: one host thread (or external locking) per
+ *    handle; calls on one handle must go to one stream at a time.
+ *
+ * State layout ("planes"): structure of arrays, plane-major, n cells per plane,
+ * contiguous: plane k occupies elements [k*n, (k+1)*n).
+ *   heat  FP64:      1 plane  of double (u)
+ *   heat  FP32:      1 plane  of float  (u)
+ *   heat  FP32_COMP: 2 planes of float  (u_hi, u_lo), value = hi + lo
+ *   Euler FP64:      3 planes of double (rho, rho*u, E)
+ *   Euler FP32:      3 planes of float
+ *   Euler FP32_COMP: 6 planes of float  (rho_hi, m_hi, E_hi, rho_lo, m_lo, E_lo)
+ * sw_pack_fp64 / sw_unpack_fp64 convert between FP64 planes and any layout.
+ */
+#ifndef SWEPT_H
+#define SWEPT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SW_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define SW_API __attribute__((visibility("default")))
+#else
+#define SW_API
+#endif
+
+/* schemes (Section 3.2) */
+#define SW_HEAT 0   /* FTCS heat equation, r = alpha dt / dx^2 */
+#define SW_EULER 1  /* 2nd-order finite volume Euler, pressure-ratio minmod limiter */
+
+/* working precision */
+#define SW_FP64 0
+#define SW_FP32 1
+#define SW_FP32_COMP 2  /* FP32 hi/lo pair with compensated (TwoSum) state update */
+
+/* boundary of the 1D domain */
+#define SW_PERIODIC 0
+#define SW_TRANSMISSIVE 1  /* zero-gradient: the ghost copies the end cell */
+
+/* decomposition (Section 3.1: Swept vs Classic) */
+#define SW_SWEPT 0    /* Up Triangle, Diamond x k, Down Triangle */
+#define SW_PERSTEP 1  /* one launch per step (Euler: per stage, the flattened form) */
+
+/* status codes */
+#define SW_OK 0
+#define SW_WARN_UNSTABLE 1       /* heat r > 1/2: runs, but FTCS is unstable */
+#define SW_ERR_BAD_ARG (-1)
+#define SW_ERR_CUDA (-2)
+#define SW_ERR_OOM (-3)
+#define SW_ERR_TIMEOUT (-4)      /* a bounded device-side wait expired */
+#define SW_ERR_NONPHYSICAL (-5)  /* Euler: rho <= 0, p <= 0 or NaN found */
+#define SW_ERR_UNSUPPORTED (-6)
+
+#define SW_MIN_TILE 4
+#define SW_MAX_TILE 1024
+
+/* The problem statement of Section 3.2: grid size, scheme, dt/dx (as r for
+ * heat, lambda = dt/dx for Euler), block (tile) base width. */
+typedef struct sw_problem {
+    int32_t scheme;     /* SW_HEAT or SW_EULER */
+    int32_t precision;  /* SW_FP64, SW_FP32 or SW_FP32_COMP */
+    int32_t boundary;   /* SW_PERIODIC or SW_TRANSMISSIVE */
+    int32_t method;     /* SW_SWEPT or SW_PERSTEP */
+    int64_t n;          /* number of cells, >= 2 * tile_width (swept) or >= 4 */
+    double r;           /* heat: alpha * dt / dx^2 (> 0) */
+    double dt_dx;       /* Euler: lambda = dt / dx (> 0) */
+    double gamma;       /* Euler: ratio of specific heats (> 1) */
+    int32_t tile_width; /* swept base width W: even, SW_MIN_TILE..SW_MAX_TILE,
+                           divides n; 0 selects the library default */
+    int32_t flags;      /* reserved, must be 0 */
+} sw_problem;
+
+typedef struct sw_handle sw_handle;
+
+/* Validate `p` and allocate the scratch the run needs (flank buffers for the
+ * swept phases, a ping-pong plane set for the per-step form, a status word) on
+ * the current device. On success *out owns that memory. Errors: SW_ERR_BAD_ARG
+ * (bad field; *out untouched), SW_ERR_OOM, SW_ERR_CUDA. Returns
+ * SW_WARN_UNSTABLE (and a valid handle) for heat with r > 1/2. */
+SW_API int sw_create(const sw_problem *p, sw_handle **out);
+
+/* Release the handle and its scratch (synchronises the device first). NULL ok. */
+SW_API void sw_destroy(sw_handle *h);
+
+/* Number of planes (of the precision's element type) and bytes of one state. */
+SW_API int sw_state_planes(const sw_problem *p);
+SW_API int64_t sw_state_bytes(const sw_problem *p);
+
+/* Advance the state in place by `nsteps` full time steps (Euler: 4 sub-steps
+ * each) on `stream`. `state` is a device pointer in the layout above. Swept:
+ * one launch per phase (Up, each Diamond, Down; Section 3.1); per-step: one
+ * launch per step (heat) or per stage (Euler). nsteps == 0 is a no-op.
+ * Errors: SW_ERR_BAD_ARG (NULL state, nsteps < 0), SW_ERR_CUDA (launch). */
+SW_API int sw_run(sw_handle *h, void *state, int64_t nsteps, void *stream);
+
+/* End-to-end form of sw_run: copy `state_in` (host memory, same layout) to the
+ * handle's device buffer, advance it, copy it back to `state_out` (host; may
+ * equal state_in), and wait for completion. Pinned host memory is fastest. */
+SW_API int sw_run_host(sw_handle *h, const void *state_in, void *state_out, int64_t nsteps,
+                void *stream);
+
+/* Conversions between FP64 planes (nplanes_fp64 = 1 heat, 3 Euler, each n
+ * doubles) and the working layout of `p`, on the device. FP32: round to
+ * nearest; FP32_COMP: hi = float(x), lo = float(x - hi). */
+SW_API int sw_pack_fp64(const sw_problem *p, const double *src_fp64, void *dst_state, void *stream);
+SW_API int sw_unpack_fp64(const sw_problem *p, const void *src_state, double *dst_fp64, void *stream);
+
+/* Deterministic FP64 sums of each conserved variable (heat: sum u; Euler: sum
+ * rho, sum m, sum E; FP32_COMP sums hi + lo), written to sums_host[0..nv) after
+ * the stream completes. Fixed-order tree: identical for identical inputs. */
+SW_API int sw_conservation(sw_handle *h, const void *state, double *sums_host, void *stream);
+
+/* Euler only: scan the state for rho <= 0, p <= 0 or NaN; latch the result.
+ * Returns SW_OK or SW_ERR_NONPHYSICAL (after synchronising `stream`); the first
+ * offending cell index is written to *cell (if non-NULL), else -1. */
+SW_API int sw_check_physical(sw_handle *h, const void *state, int64_t *cell, void *stream);
+
+/* Synchronise `stream` and return the latched device status (then clear it). */
+SW_API int sw_sync_status(sw_handle *h, void *stream);
+
+/* Number of kernel launches the last sw_run on this handle issued. */
+SW_API int64_t sw_last_launch_count(const sw_handle *h);
+
+/* Per-launch tracing. sw_set_timing(h, capacity) makes every following sw_run
+ * record a CUDA event pair around each of its first `capacity` launches, on
+ * the run's stream (capacity 0 turns it off; SW_ERR_OOM/SW_ERR_CUDA if the
+ * events cannot be created). sw_launch_times waits for those events and writes
+ * up to `cap` durations in milliseconds to ms[] and the launch kinds to kind[]
+ * (0 Up Triangle, 1 Diamond, 2 Down Triangle, 3 per-step kernel); it returns
+ * the number written, or a negative status. */
+SW_API int sw_set_timing(sw_handle *h, int64_t capacity);
+SW_API int64_t sw_launch_times(sw_handle *h, float *ms, int32_t *kind, int64_t cap);
+
+/* Tile width actually used by the handle (after defaults). */
+SW_API int32_t sw_tile_width(const sw_handle *h);
+
+SW_API const char *sw_status_string(int status);
+SW_API int sw_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWEPT_H */

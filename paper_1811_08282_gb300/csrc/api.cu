@@ -1,0 +1,600 @@
+// api.cu -- C ABI of libswept.so (declared in include/swept.h): problem
+// validation, scratch ownership, the host-side phase planner of the swept rule
+// (Section 3.1) and the per-step loop (Section 3.3), plus conversion,
+// conservation and positivity utilities. All compute runs in the kernels of
+// swept_phase.cuh and perstep.cuh; this file only plans and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/swept.h"
+#include "perstep.cuh"
+#include "schemes.cuh"
+#include "swept_phase.cuh"
+
+using namespace sw;
+
+struct sw_handle {
+    sw_problem prob;
+    int W = 0, H = 0, threads = 0;
+    int64_t M = 0, S = 0;       // tiles, structures per flank buffer
+    size_t esize = 0;           // element size of the working precision
+    int nsnap = 0, nio = 0;     // snapshot fields, state planes
+    size_t smem = 0;            // dynamic shared memory per swept CTA
+    void *flank[2] = {nullptr, nullptr};
+    size_t flank_bytes = 0;
+    void *scratch = nullptr;    // per-step ping-pong planes / Q* planes
+    size_t scratch_bytes = 0;
+    void *dev_state = nullptr;  // device copy used by sw_run_host
+    int *d_status = nullptr;    // [0] latched status, [1..2] first bad cell (int64)
+    double *d_partial = nullptr;
+    double *d_sums = nullptr;
+    HeatParams hp{};
+    EulerParams ep{};
+    int64_t last_launches = 0;
+    int device = 0;
+    // tracing: event pairs around the first `ev_cap` launches of a run
+    std::vector<cudaEvent_t> events;
+    std::vector<int32_t> kinds;
+    int64_t ev_cap = 0, ev_used = 0;
+};
+
+namespace {
+
+constexpr int kRedBlocks = 1024;
+constexpr int kRedThreads = 256;
+
+int scheme_nv(const sw_problem &p) { return p.scheme == SW_HEAT ? 1 : 3; }
+
+int planes_of(const sw_problem &p) {
+    const int nv = scheme_nv(p);
+    return p.precision == SW_FP32_COMP ? 2 * nv : nv;
+}
+
+size_t elem_size(const sw_problem &p) { return p.precision == SW_FP64 ? sizeof(double) : sizeof(float); }
+
+int validate(const sw_problem *p) {
+    if (!p) return SW_ERR_BAD_ARG;
+    if (p->scheme != SW_HEAT && p->scheme != SW_EULER) return SW_ERR_BAD_ARG;
+    if (p->precision < SW_FP64 || p->precision > SW_FP32_COMP) return SW_ERR_BAD_ARG;
+    if (p->boundary != SW_PERIODIC && p->boundary != SW_TRANSMISSIVE) return SW_ERR_BAD_ARG;
+    if (p->method != SW_SWEPT && p->method != SW_PERSTEP) return SW_ERR_BAD_ARG;
+    if (p->flags != 0) return SW_ERR_BAD_ARG;
+    if (p->n < 4 || p->n > (int64_t(1) << 40)) return SW_ERR_BAD_ARG;
+    if (p->scheme == SW_HEAT) {
+        if (!(p->r > 0.0) || !(p->r < 1e6)) return SW_ERR_BAD_ARG;
+    } else {
+        if (!(p->dt_dx > 0.0) || !(p->gamma > 1.0) || !(p->gamma < 1e6)) return SW_ERR_BAD_ARG;
+    }
+    if (p->method == SW_SWEPT) {
+        const int W = p->tile_width == 0 ? 0 : p->tile_width;
+        if (W != 0) {
+            if (W < SW_MIN_TILE || W > SW_MAX_TILE || (W & 1)) return SW_ERR_BAD_ARG;
+            if (p->n % W != 0 || p->n < 2 * (int64_t)W) return SW_ERR_BAD_ARG;
+        }
+    } else if (p->tile_width != 0 && (p->tile_width < 0)) {
+        return SW_ERR_BAD_ARG;
+    }
+    return SW_OK;
+}
+
+// Default base width: the largest of 1024, 512, ..., 4 that divides n with at
+// least two tiles (Section 5 recommends large blocks, 768-1024).
+int default_width(const sw_problem &p) {
+    for (int W = SW_MAX_TILE; W >= SW_MIN_TILE; W >>= 1)
+        if (p.n % W == 0 && p.n >= 2 * (int64_t)W) return W;
+    return 0;
+}
+
+int swept_threads(int W) {
+    int t = W / 2;
+    t = (t + 31) / 32 * 32;
+    return std::min(512, std::max(32, t));
+}
+
+template <class P> size_t swept_smem(int W) {
+    return (size_t(P::NROW) * (W + 2) + size_t(P::NSNAP) * 2 * W) * sizeof(typename P::T);
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SW_OK;
+    if (e == cudaErrorMemoryAllocation) return SW_ERR_OOM;
+    return SW_ERR_CUDA;
+}
+
+template <class P> int prepare_swept_kernel(size_t smem) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_swept_phase<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return SW_OK;
+}
+
+// Record the start / end event of launch `i` of the current run (tracing only).
+inline void trace_begin(sw_handle *h, int64_t i, int32_t kind, cudaStream_t st) {
+    if (i < h->ev_cap) {
+        cudaEventRecord(h->events[2 * i], st);
+        h->kinds[i] = kind;
+    }
+}
+inline void trace_end(sw_handle *h, int64_t i, cudaStream_t st) {
+    if (i < h->ev_cap) {
+        cudaEventRecord(h->events[2 * i + 1], st);
+        h->ev_used = i + 1;
+    }
+}
+
+template <class P>
+int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st) {
+    using T = typename P::T;
+    const int H = h->H, W = h->W;
+    const int64_t P_last = (L + H - 1) / H;
+    const bool periodic = h->prob.boundary == SW_PERIODIC;
+    int64_t launches = 0;
+    for (int64_t p = 0; p <= P_last; ++p) {
+        PhaseArgs<T> a{};
+        a.n = h->prob.n;
+        a.W = W;
+        a.H = H;
+        a.periodic = periodic ? 1 : 0;
+        // the kernel needs only "Up or not" and the parity of p
+        a.p = (p == 0) ? 0 : (int)(2 - (p & 1));
+        a.F = p * H;
+        a.lower = (p == 0) ? 0 : (int)std::min<int64_t>(H, L - (p - 1) * H);
+        a.upper = (p == P_last) ? 0 : (int)std::min<int64_t>(H - 1, L - p * H);
+        a.write_lower = (p == P_last) ? 1 : 0;
+        a.write_upper = (a.upper > 0 && p * H + a.upper == L) ? 1 : 0;
+        a.tiles = h->M;
+        a.nstruct = (p & 1) ? (periodic ? h->M : h->M + 1) : h->M;
+        a.nstruct_max = h->S;
+        a.flank_in = (p == 0) ? nullptr : reinterpret_cast<const T *>(h->flank[(p - 1) & 1]);
+        a.flank_out = reinterpret_cast<T *>(h->flank[p & 1]);
+        a.state = reinterpret_cast<T *>(state);
+        typename P::Params prm;
+        if constexpr (std::is_same<typename P::Params, HeatParams>::value) prm = h->hp;
+        else prm = h->ep;
+        trace_begin(h, launches, p == 0 ? 0 : (p == P_last ? 2 : 1), st);
+        k_swept_phase<P><<<(unsigned)a.nstruct, h->threads, h->smem, st>>>(a, prm);
+        trace_end(h, launches, st);
+        ++launches;
+    }
+    h->last_launches = launches;
+    return cuda_status(cudaGetLastError());
+}
+
+unsigned grid_for(int64_t work, int threads, int cap) {
+    int64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+int launch_perstep_heat(sw_handle *h, void *state, int64_t nsteps, cudaStream_t st) {
+    const int64_t n = h->prob.n;
+    const int periodic = h->prob.boundary == SW_PERIODIC;
+    const size_t bytes = size_t(planes_of(h->prob)) * n * h->esize;
+    void *bufs[2] = {state, h->scratch};
+    int64_t launches = 0;
+    const int cap = 152 * 16;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        void *in = bufs[s & 1], *out = bufs[(s + 1) & 1];
+        trace_begin(h, launches, 3, st);
+        switch (h->prob.precision) {
+        case SW_FP64:
+            if (n % 2 == 0)
+                k_heat_step<OpsD, 2><<<grid_for(n / 2, 256, cap), 256, 0, st>>>(
+                    (const double *)in, (double *)out, n, h->hp.r, periodic);
+            else
+                k_heat_step<OpsD, 1><<<grid_for(n, 256, cap), 256, 0, st>>>((const double *)in, (double *)out,
+                                                                             n, h->hp.r, periodic);
+            break;
+        case SW_FP32:
+            if (n % 4 == 0)
+                k_heat_step<OpsF, 4><<<grid_for(n / 4, 256, cap), 256, 0, st>>>((const float *)in, (float *)out,
+                                                                                 n, h->hp.rf, periodic);
+            else
+                k_heat_step<OpsF, 1><<<grid_for(n, 256, cap), 256, 0, st>>>((const float *)in, (float *)out, n,
+                                                                             h->hp.rf, periodic);
+            break;
+        default:
+            if (n % 4 == 0)
+                k_heat_step_comp<4><<<grid_for(n / 4, 256, cap), 256, 0, st>>>(
+                    (const float *)in, (float *)out, n, h->hp.rf, h->hp.rf_lo, periodic);
+            else
+                k_heat_step_comp<1><<<grid_for(n, 256, cap), 256, 0, st>>>((const float *)in, (float *)out, n,
+                                                                            h->hp.rf, h->hp.rf_lo, periodic);
+            break;
+        }
+        trace_end(h, launches, st);
+        ++launches;
+    }
+    if (nsteps & 1) {
+        cudaError_t e = cudaMemcpyAsync(state, h->scratch, bytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    h->last_launches = launches;
+    return cuda_status(cudaGetLastError());
+}
+
+template <class O, bool COMP>
+int launch_perstep_euler_t(sw_handle *h, void *state, int64_t nsteps, cudaStream_t st) {
+    using T = typename O::T;
+    const int64_t n = h->prob.n;
+    const int periodic = h->prob.boundary == SW_PERIODIC;
+    const int B = 256;
+    const size_t smem = (size_t(3) * (B + 4) + (B + 4) + (B + 2) + size_t(3) * (B + 1)) * sizeof(T);
+    const unsigned grid = (unsigned)((n + B - 1) / B);
+    T *q = reinterpret_cast<T *>(state);
+    T *s = reinterpret_cast<T *>(h->scratch);
+    for (int64_t k = 0; k < nsteps; ++k) {
+        trace_begin(h, 2 * k, 3, st);
+        k_euler_stage<O, false, COMP><<<grid, B, smem, st>>>(q, s, n, h->ep, periodic);
+        trace_end(h, 2 * k, st);
+        trace_begin(h, 2 * k + 1, 3, st);
+        k_euler_stage<O, true, COMP><<<grid, B, smem, st>>>(q, s, n, h->ep, periodic);
+        trace_end(h, 2 * k + 1, st);
+    }
+    h->last_launches = 2 * nsteps;
+    return cuda_status(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- utilities
+__global__ void k_pack(const double *__restrict__ src, void *__restrict__ dst, int64_t count, int prec) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = src[i];
+        if (prec == SW_FP64) {
+            reinterpret_cast<double *>(dst)[i] = x;
+        } else if (prec == SW_FP32) {
+            reinterpret_cast<float *>(dst)[i] = __double2float_rn(x);
+        } else {
+            const float hi = __double2float_rn(x);
+            const float lo = __double2float_rn(x - (double)hi);
+            // layout: all hi planes, then all lo planes
+            reinterpret_cast<float *>(dst)[i] = hi;
+            reinterpret_cast<float *>(dst)[count + i] = lo;
+        }
+    }
+}
+
+__global__ void k_unpack(const void *__restrict__ src, double *__restrict__ dst, int64_t count, int prec) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (prec == SW_FP64) dst[i] = reinterpret_cast<const double *>(src)[i];
+        else if (prec == SW_FP32) dst[i] = (double)reinterpret_cast<const float *>(src)[i];
+        else
+            dst[i] = (double)reinterpret_cast<const float *>(src)[i] +
+                     (double)reinterpret_cast<const float *>(src)[count + i];
+    }
+}
+
+// Deterministic FP64 sum of plane v: block b sums a fixed contiguous chunk with a
+// fixed tree; the partials are summed in a fixed order by one block.
+__device__ __forceinline__ double state_value(const void *st, int64_t n, int v, int64_t i, int prec, int nv) {
+    if (prec == SW_FP64) return reinterpret_cast<const double *>(st)[v * n + i];
+    const float *f = reinterpret_cast<const float *>(st);
+    if (prec == SW_FP32) return (double)f[v * n + i];
+    return (double)f[v * n + i] + (double)f[(nv + v) * n + i];
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_sum_partial(const void *st, int64_t n, int nv, int prec,
+                                                             double *partial) {
+    __shared__ double red[kRedThreads];
+    const int v = blockIdx.y;
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * chunk;
+    const int64_t hi = lo + chunk < n ? lo + chunk : n;
+    double acc = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += state_value(st, n, v, i, prec, nv);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[v * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_final(const double *partial, int nblocks, int nv, double *out) {
+    __shared__ double red[kRedThreads];
+    for (int v = 0; v < nv; ++v) {
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += partial[v * nblocks + i];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[v] = red[0];
+        __syncthreads();
+    }
+}
+
+// Positivity / NaN scan of an Euler state; records the smallest bad index.
+__global__ void k_check_physical(const void *st, int64_t n, int prec, double gamma,
+                                 unsigned long long *first_bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double rho = state_value(st, n, 0, i, prec, 3);
+        const double m = state_value(st, n, 1, i, prec, 3);
+        const double E = state_value(st, n, 2, i, prec, 3);
+        const double p = (gamma - 1.0) * (E - 0.5 * m * (m / rho));
+        const bool ok = rho > 0.0 && p > 0.0 && isfinite(rho) && isfinite(m) && isfinite(E);
+        if (!ok) atomicMin(first_bad, (unsigned long long)i);
+    }
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+int sw_abi_version(void) { return SW_ABI_VERSION; }
+
+const char *sw_status_string(int s) {
+    switch (s) {
+    case SW_OK: return "ok";
+    case SW_WARN_UNSTABLE: return "warning: heat r > 1/2, FTCS is unstable";
+    case SW_ERR_BAD_ARG: return "bad argument";
+    case SW_ERR_CUDA: return "CUDA error";
+    case SW_ERR_OOM: return "out of device memory";
+    case SW_ERR_TIMEOUT: return "device-side wait timed out";
+    case SW_ERR_NONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or NaN)";
+    case SW_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+    }
+}
+
+int sw_state_planes(const sw_problem *p) {
+    if (validate(p) != SW_OK) return SW_ERR_BAD_ARG;
+    return planes_of(*p);
+}
+
+int64_t sw_state_bytes(const sw_problem *p) {
+    if (validate(p) != SW_OK) return SW_ERR_BAD_ARG;
+    return int64_t(planes_of(*p)) * p->n * int64_t(elem_size(*p));
+}
+
+int sw_create(const sw_problem *p, sw_handle **out) {
+    if (!out) return SW_ERR_BAD_ARG;
+    int rc = validate(p);
+    if (rc != SW_OK) return rc;
+    sw_handle *h = new (std::nothrow) sw_handle();
+    if (!h) return SW_ERR_OOM;
+    h->prob = *p;
+    cudaGetDevice(&h->device);
+    h->esize = elem_size(*p);
+    h->nio = planes_of(*p);
+    // scheme constants, rounded once on the host
+    h->hp.r = p->r;
+    h->hp.rf = (float)p->r;
+    h->hp.rf_lo = (float)(p->r - (double)h->hp.rf);
+    h->ep.gamma = p->gamma;
+    h->ep.gm1 = p->gamma - 1.0;
+    h->ep.lam = p->dt_dx;
+    h->ep.hlam = 0.5 * p->dt_dx;
+    h->ep.gammaf = (float)p->gamma;
+    h->ep.gm1f = (float)(p->gamma - 1.0);
+    h->ep.lamf = (float)p->dt_dx;
+    h->ep.hlamf = (float)(0.5 * p->dt_dx);
+
+    auto fail = [&](int code) {
+        sw_destroy(h);
+        return code;
+    };
+    cudaError_t e;
+    if (p->method == SW_SWEPT) {
+        h->W = p->tile_width ? p->tile_width : default_width(*p);
+        if (h->W == 0) return fail(SW_ERR_BAD_ARG);
+        h->H = h->W / 2;
+        h->M = p->n / h->W;
+        h->S = h->M + 1;
+        h->threads = swept_threads(h->W);
+        int prc = SW_OK;
+        if (p->scheme == SW_HEAT) {
+            switch (p->precision) {
+            case SW_FP64: h->nsnap = HeatPolicy<0>::NSNAP; h->smem = swept_smem<HeatPolicy<0>>(h->W);
+                prc = prepare_swept_kernel<HeatPolicy<0>>(h->smem); break;
+            case SW_FP32: h->nsnap = HeatPolicy<1>::NSNAP; h->smem = swept_smem<HeatPolicy<1>>(h->W);
+                prc = prepare_swept_kernel<HeatPolicy<1>>(h->smem); break;
+            default: h->nsnap = HeatPolicy<2>::NSNAP; h->smem = swept_smem<HeatPolicy<2>>(h->W);
+                prc = prepare_swept_kernel<HeatPolicy<2>>(h->smem); break;
+            }
+        } else {
+            switch (p->precision) {
+            case SW_FP64: h->nsnap = EulerPolicy<0>::NSNAP; h->smem = swept_smem<EulerPolicy<0>>(h->W);
+                prc = prepare_swept_kernel<EulerPolicy<0>>(h->smem); break;
+            case SW_FP32: h->nsnap = EulerPolicy<1>::NSNAP; h->smem = swept_smem<EulerPolicy<1>>(h->W);
+                prc = prepare_swept_kernel<EulerPolicy<1>>(h->smem); break;
+            default: h->nsnap = EulerPolicyComp::NSNAP; h->smem = swept_smem<EulerPolicyComp>(h->W);
+                prc = prepare_swept_kernel<EulerPolicyComp>(h->smem); break;
+            }
+        }
+        if (prc != SW_OK) return fail(prc);
+        if (h->smem > 227 * 1024) return fail(SW_ERR_UNSUPPORTED);
+        h->flank_bytes = size_t(h->nsnap) * size_t(h->S) * 2 * h->W * h->esize;
+        for (int i = 0; i < 2; ++i) {
+            e = cudaMalloc(&h->flank[i], h->flank_bytes);
+            if (e != cudaSuccess) return fail(cuda_status(e));
+        }
+    } else {
+        if (p->scheme == SW_HEAT) h->scratch_bytes = size_t(h->nio) * p->n * h->esize;
+        else h->scratch_bytes = size_t(3) * p->n * h->esize;  // Q* planes
+        e = cudaMalloc(&h->scratch, h->scratch_bytes);
+        if (e != cudaSuccess) return fail(cuda_status(e));
+    }
+    e = cudaMalloc(&h->d_status, 4 * sizeof(int));
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    e = cudaMemset(h->d_status, 0, 4 * sizeof(int));
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    e = cudaMalloc(&h->d_partial, size_t(kRedBlocks) * 3 * sizeof(double));
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    e = cudaMalloc(&h->d_sums, 4 * sizeof(double));
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    *out = h;
+    if (p->scheme == SW_HEAT && p->r > 0.5) return SW_WARN_UNSTABLE;
+    return SW_OK;
+}
+
+void sw_destroy(sw_handle *h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    cudaFree(h->flank[0]);
+    cudaFree(h->flank[1]);
+    cudaFree(h->scratch);
+    cudaFree(h->dev_state);
+    cudaFree(h->d_status);
+    cudaFree(h->d_partial);
+    cudaFree(h->d_sums);
+    delete h;
+}
+
+int32_t sw_tile_width(const sw_handle *h) { return h ? h->W : 0; }
+
+int64_t sw_last_launch_count(const sw_handle *h) { return h ? h->last_launches : 0; }
+
+int sw_set_timing(sw_handle *h, int64_t capacity) {
+    if (!h || capacity < 0 || capacity > (int64_t(1) << 24)) return SW_ERR_BAD_ARG;
+    while ((int64_t)h->events.size() < 2 * capacity) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return cuda_status(err);
+        h->events.push_back(e);
+    }
+    h->kinds.assign((size_t)capacity, 0);
+    h->ev_cap = capacity;
+    h->ev_used = 0;
+    return SW_OK;
+}
+
+int64_t sw_launch_times(sw_handle *h, float *ms, int32_t *kind, int64_t cap) {
+    if (!h || cap < 0 || (cap > 0 && (!ms || !kind))) return SW_ERR_BAD_ARG;
+    const int64_t cnt = std::min(cap, h->ev_used);
+    for (int64_t i = 0; i < cnt; ++i) {
+        cudaError_t e = cudaEventSynchronize(h->events[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaEventElapsedTime(&ms[i], h->events[2 * i], h->events[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_status(e);
+        kind[i] = h->kinds[i];
+    }
+    return cnt;
+}
+
+int sw_run(sw_handle *h, void *state, int64_t nsteps, void *stream) {
+    if (!h || !state || nsteps < 0) return SW_ERR_BAD_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    h->last_launches = 0;
+    h->ev_used = 0;
+    if (nsteps == 0) return SW_OK;
+    const sw_problem &p = h->prob;
+    if (p.method == SW_SWEPT) {
+        const int64_t L = nsteps * (p.scheme == SW_HEAT ? 1 : 4);
+        if (p.scheme == SW_HEAT) {
+            switch (p.precision) {
+            case SW_FP64: return launch_swept<HeatPolicy<0>>(h, state, L, st);
+            case SW_FP32: return launch_swept<HeatPolicy<1>>(h, state, L, st);
+            default: return launch_swept<HeatPolicy<2>>(h, state, L, st);
+            }
+        }
+        switch (p.precision) {
+        case SW_FP64: return launch_swept<EulerPolicy<0>>(h, state, L, st);
+        case SW_FP32: return launch_swept<EulerPolicy<1>>(h, state, L, st);
+        default: return launch_swept<EulerPolicyComp>(h, state, L, st);
+        }
+    }
+    if (p.scheme == SW_HEAT) return launch_perstep_heat(h, state, nsteps, st);
+    switch (p.precision) {
+    case SW_FP64: return launch_perstep_euler_t<OpsD, false>(h, state, nsteps, st);
+    case SW_FP32: return launch_perstep_euler_t<OpsF, false>(h, state, nsteps, st);
+    default: return launch_perstep_euler_t<OpsF, true>(h, state, nsteps, st);
+    }
+}
+
+int sw_run_host(sw_handle *h, const void *state_in, void *state_out, int64_t nsteps, void *stream) {
+    if (!h || !state_in || !state_out || nsteps < 0) return SW_ERR_BAD_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = size_t(h->nio) * h->prob.n * h->esize;
+    if (!h->dev_state) {
+        cudaError_t e = cudaMalloc(&h->dev_state, bytes);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    cudaError_t e = cudaMemcpyAsync(h->dev_state, state_in, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    int rc = sw_run(h, h->dev_state, nsteps, stream);
+    if (rc != SW_OK) return rc;
+    e = cudaMemcpyAsync(state_out, h->dev_state, bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(cudaStreamSynchronize(st));
+}
+
+int sw_pack_fp64(const sw_problem *p, const double *src, void *dst, void *stream) {
+    if (validate(p) != SW_OK || !src || !dst) return SW_ERR_BAD_ARG;
+    const int64_t count = int64_t(scheme_nv(*p)) * p->n;
+    k_pack<<<grid_for(count, 256, 152 * 8), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(src, dst, count,
+                                                                                               p->precision);
+    return cuda_status(cudaGetLastError());
+}
+
+int sw_unpack_fp64(const sw_problem *p, const void *src, double *dst, void *stream) {
+    if (validate(p) != SW_OK || !src || !dst) return SW_ERR_BAD_ARG;
+    const int64_t count = int64_t(scheme_nv(*p)) * p->n;
+    k_unpack<<<grid_for(count, 256, 152 * 8), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(src, dst, count,
+                                                                                                 p->precision);
+    return cuda_status(cudaGetLastError());
+}
+
+int sw_conservation(sw_handle *h, const void *state, double *sums_host, void *stream) {
+    if (!h || !state || !sums_host) return SW_ERR_BAD_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int nv = scheme_nv(h->prob);
+    dim3 grid(kRedBlocks, nv);
+    k_sum_partial<<<grid, kRedThreads, 0, st>>>(state, h->prob.n, nv, h->prob.precision, h->d_partial);
+    k_sum_final<<<1, kRedThreads, 0, st>>>(h->d_partial, kRedBlocks, nv, h->d_sums);
+    cudaError_t e = cudaMemcpyAsync(sums_host, h->d_sums, nv * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(cudaStreamSynchronize(st));
+}
+
+int sw_check_physical(sw_handle *h, const void *state, int64_t *cell, void *stream) {
+    if (!h || !state) return SW_ERR_BAD_ARG;
+    if (h->prob.scheme != SW_EULER) return SW_ERR_BAD_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned long long *bad = reinterpret_cast<unsigned long long *>(h->d_partial);
+    cudaError_t e = cudaMemsetAsync(bad, 0xff, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_status(e);
+    k_check_physical<<<grid_for(h->prob.n, 256, 152 * 8), 256, 0, st>>>(state, h->prob.n, h->prob.precision,
+                                                                          h->prob.gamma, bad);
+    unsigned long long host = 0;
+    e = cudaMemcpyAsync(&host, bad, sizeof(host), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    const bool ok = host == ~0ull;
+    if (cell) *cell = ok ? -1 : (int64_t)host;
+    if (!ok) {
+        const int code = SW_ERR_NONPHYSICAL;
+        cudaMemcpy(h->d_status, &code, sizeof(int), cudaMemcpyHostToDevice);
+        return SW_ERR_NONPHYSICAL;
+    }
+    return SW_OK;
+}
+
+int sw_sync_status(sw_handle *h, void *stream) {
+    if (!h) return SW_ERR_BAD_ARG;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_status(e);
+    int code = 0;
+    e = cudaMemcpy(&code, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (code != 0) cudaMemset(h->d_status, 0, sizeof(int));
+    return code;
+}
+
+}  // extern "C"

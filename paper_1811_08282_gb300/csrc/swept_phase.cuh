@@ -1,0 +1,186 @@
+// swept_phase.cuh -- one launch = one swept phase (Section 3.1, Fig. 1) over all
+// structures (triangles / diamonds) of that phase, one CTA per structure.
+//
+// Geometry (H = W/2, tiles [tW, tW+W), level = sub-step index):
+//   phase p has full level F = p*H and centres c = t*W + H (p even, tile centred)
+//   or c = t*W (p odd, centred on the seam between tiles t-1 and t).
+//   lower half (p >= 1): levels F-H+i, i = 1..H, cells [c-i, c+i-1]   (widening)
+//   upper half:          levels F+i,   i = 1..H-1, cells [c-H+i, c+H-1-i] (narrowing)
+//   Phase 0 = Up Triangle (upper half only, from the initial row); the phases
+//   with both halves are Diamonds; the last phase is the Down Triangle (lower
+//   half only). Lower(p) and upper(p-1) tile every level, so each (cell, level)
+//   is computed exactly once: the swept rule does no redundant work.
+// Communication (Fig. 1b, 1d): after its upper half a structure has exported,
+// for every level F+j (j = 0..H-1), the two outermost cells on each side (its
+// "flanks"); the lower half of the next phase at centre c' takes the right
+// flank of the structure at c'-H and the left flank of the one at c'+H. Flanks
+// travel through HBM between launches (global buffers, double-buffered by phase).
+// A run that stops at a level L between full levels truncates the last upper
+// half and the Down Triangle at L, so any number of sub-steps needs no extra
+// per-step launches.
+#pragma once
+#include "common.cuh"
+
+namespace sw {
+
+template <class T> struct PhaseArgs {
+    int64_t n;           // cells
+    int W, H;
+    int periodic;        // 1 periodic, 0 transmissive
+    int p;               // phase index
+    int64_t F;           // full level of this phase (p*H)
+    int lower;           // lower-half levels computed (0 for p == 0)
+    int upper;           // upper-half levels computed
+    int write_lower;     // lower half ends at the final level: store its top row
+    int write_upper;     // upper half ends at the final level: store its top row
+    int64_t nstruct;     // structures in this phase
+    int64_t nstruct_max; // structures per flank buffer
+    int64_t tiles;       // M = n / W
+    const T *flank_in;   // previous phase's flanks
+    T *flank_out;        // this phase's flanks
+    T *state;            // state planes (layout of the policy)
+};
+
+// Flank buffer element ((f * S + b) * 2 + side) * W + (2*j + k):
+// field f, structure b, side 0 = left / 1 = right, level offset j, cell k of the pair.
+template <class T>
+__device__ __forceinline__ int64_t flank_off(int64_t S, int W, int f, int64_t b, int side) {
+    return ((f * S + b) * 2 + side) * (int64_t)W;
+}
+
+template <class P>
+__global__ void __launch_bounds__(512) k_swept_phase(PhaseArgs<typename P::T> a, typename P::Params prm) {
+    using T = typename P::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *row = reinterpret_cast<T *>(smem_raw);
+    const int W = a.W, H = a.H;
+    const int rs = W + 2;                 // row stride (positions 0..W+1)
+    T *stage = row + P::NROW * rs;        // [NSNAP][2 sides][W]
+    const int ss = 2 * W;                 // stage field stride
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t b = blockIdx.x;
+    const int64_t n = a.n;
+    const int64_t c = (a.p & 1) ? b * W : b * W + H;
+    const int64_t base = c - H - 1;       // cell of row position 0
+
+    // valid row positions (transmissive domains clip to [0, n))
+    int slo = 0, shi = W + 1;
+    if (!a.periodic) {
+        if (base < 0) slo = (int)(-base);
+        if (base + W + 1 > n - 1) shi = (int)(n - 1 - base);
+    }
+    auto cell = [&](int s) -> int64_t { return a.periodic ? wrap_index(base + s, n) : base + s; };
+    auto ghost_l = [&](int s) -> bool { return !a.periodic && base + s == 0; };
+    auto ghost_r = [&](int s) -> bool { return !a.periodic && base + s == n - 1; };
+
+    if (a.p == 0) {
+        // Up Triangle: the initial row [c-H, c+H) at level 0 (always inside the domain)
+        for (int s = 1 + tid; s <= W; s += nt) {
+            P::load_state(row, rs, s, a.state, n, base + s);
+        }
+        __syncthreads();
+        // flank entries of level 0 (j = 0): cells s = 1, 2 (left) and W-1, W (right)
+        if (tid < 4) {
+            const int side = tid >> 1, k = tid & 1;
+            const int s = side == 0 ? 1 + k : W - 1 + k;
+            P::snap_out(row, rs, s, 0, stage, ss, side * W + k);
+        }
+        __syncthreads();
+    } else {
+        // neighbours in phase p-1: left has centre c-H, right has centre c+H
+        int64_t lb, rb;
+        if (a.p & 1) { lb = b - 1; rb = b; }   // seam centred: tiles b-1 and b
+        else { lb = b; rb = b + 1; }           // tile centred: seams b and b+1
+        bool has_l = true, has_r = true;
+        if (a.periodic) {
+            const int64_t M = a.tiles;
+            lb = (lb + M) % M;
+            rb = rb % M;
+        } else {
+            if (a.p & 1) { has_l = b > 0; has_r = b < a.tiles; }
+        }
+        // stage: side 0 <- left neighbour's right flank, side 1 <- right neighbour's left flank
+        const int64_t S = a.nstruct_max;
+        for (int f = 0; f < P::NSNAP; ++f) {
+            if (has_l) {
+                const T *src = a.flank_in + flank_off<T>(S, W, f, lb, 1);
+                for (int e = tid; e < W; e += nt) stage[f * ss + e] = src[e];
+            }
+            if (has_r) {
+                const T *src = a.flank_in + flank_off<T>(S, W, f, rb, 0);
+                for (int e = tid; e < W; e += nt) stage[f * ss + W + e] = src[e];
+            }
+        }
+        __syncthreads();
+        // inject the flank pair for step i (level F-H+i-1) into the row
+        auto inject = [&](int i) {
+            if (tid < 4) {
+                const int side = tid >> 1, k = tid & 1;
+                const int s = side == 0 ? H - i + k : H + i + k;
+                const bool ok = side == 0 ? has_l : has_r;
+                if (ok && s >= slo && s <= shi)
+                    P::snap_in(row, rs, s, a.F - H + i - 1, stage, ss, side * W + 2 * (i - 1) + k);
+            }
+        };
+        if (P::INJECT_AHEAD && a.lower > 0) {
+            inject(1);
+            __syncthreads();
+        }
+        for (int i = 1; i <= a.lower; ++i) {
+            const int64_t lev = a.F - H + i - 1;  // level read; level lev+1 written
+            if (!P::INJECT_AHEAD) {
+                inject(i);
+                __syncthreads();
+            }
+            int lo = H + 1 - i, hi = H + i;
+            if (lo < slo) lo = slo;
+            if (hi > shi) hi = shi;
+            const bool last = (i == a.lower);
+            for (int s = lo + tid; s <= hi; s += nt) {
+                P::step(prm, row, rs, s, lev, ghost_l(s), ghost_r(s));
+                if (i == H && a.upper > 0) {  // full level F reached: flank entries j = 0
+                    if (s == 1) P::snap_out(row, rs, s, lev + 1, stage, ss, 0);
+                    if (s == 2) P::snap_out(row, rs, s, lev + 1, stage, ss, 1);
+                    if (s == W - 1) P::snap_out(row, rs, s, lev + 1, stage, ss, W);
+                    if (s == W) P::snap_out(row, rs, s, lev + 1, stage, ss, W + 1);
+                }
+                if (last && a.write_lower) P::store_state(row, rs, s, lev + 1, a.state, n, cell(s));
+            }
+            if (P::INJECT_AHEAD && i < a.lower) inject(i + 1);
+            __syncthreads();
+        }
+    }
+
+    // upper half: levels F+1 .. F+upper on the narrowing window
+    for (int i = 1; i <= a.upper; ++i) {
+        const int64_t lev = a.F + i - 1;
+        int lo = 1 + i, hi = W - i;
+        if (lo < slo) lo = slo;
+        if (hi > shi) hi = shi;
+        const bool last = (i == a.upper);
+        for (int s = lo + tid; s <= hi; s += nt) {
+            P::step(prm, row, rs, s, lev, ghost_l(s), ghost_r(s));
+            if (s == 1 + i) P::snap_out(row, rs, s, lev + 1, stage, ss, 2 * i);
+            if (s == 2 + i) P::snap_out(row, rs, s, lev + 1, stage, ss, 2 * i + 1);
+            if (s == W - 1 - i) P::snap_out(row, rs, s, lev + 1, stage, ss, W + 2 * i);
+            if (s == W - i) P::snap_out(row, rs, s, lev + 1, stage, ss, W + 2 * i + 1);
+            if (last && a.write_upper) P::store_state(row, rs, s, lev + 1, a.state, n, cell(s));
+        }
+        __syncthreads();
+    }
+
+    // publish this structure's flanks for the next phase
+    if (a.upper > 0 && a.flank_out) {
+        const int64_t S = a.nstruct_max;
+        for (int f = 0; f < P::NSNAP; ++f) {
+            T *dl = a.flank_out + flank_off<T>(S, W, f, b, 0);
+            T *dr = a.flank_out + flank_off<T>(S, W, f, b, 1);
+            for (int e = tid; e < W; e += nt) {
+                dl[e] = stage[f * ss + e];
+                dr[e] = stage[f * ss + W + e];
+            }
+        }
+    }
+}
+
+}  // namespace sw

@@ -1,0 +1,288 @@
+"""Thin ctypes binding of libswept.so (include/swept.h), same names as the C ABI.
+
+Argument marshalling only: every step of the swept and per-step paths runs in
+the CUDA kernels of the library. torch tensors are accepted where the C ABI
+takes device pointers (their ``data_ptr()``), and streams default to
+``torch.cuda.current_stream()``. There is no CPU fallback: if the library is
+missing or fails to load, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libswept.so")
+
+SW_HEAT, SW_EULER = 0, 1
+SW_FP64, SW_FP32, SW_FP32_COMP = 0, 1, 2
+SW_PERIODIC, SW_TRANSMISSIVE = 0, 1
+SW_SWEPT, SW_PERSTEP = 0, 1
+SW_OK, SW_WARN_UNSTABLE = 0, 1
+SW_ERR_BAD_ARG, SW_ERR_CUDA, SW_ERR_OOM = -1, -2, -3
+SW_ERR_TIMEOUT, SW_ERR_NONPHYSICAL, SW_ERR_UNSUPPORTED = -4, -5, -6
+SW_MIN_TILE, SW_MAX_TILE = 4, 1024
+
+# every symbol declared in include/swept.h
+EXPORTS = (
+    "sw_create", "sw_destroy", "sw_state_planes", "sw_state_bytes", "sw_run", "sw_run_host",
+    "sw_pack_fp64", "sw_unpack_fp64", "sw_conservation", "sw_check_physical", "sw_sync_status",
+    "sw_last_launch_count", "sw_tile_width", "sw_status_string", "sw_abi_version",
+    "sw_set_timing", "sw_launch_times",
+)
+
+
+class sw_problem(ctypes.Structure):
+    _fields_ = [
+        ("scheme", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("boundary", ctypes.c_int32),
+        ("method", ctypes.c_int32),
+        ("n", ctypes.c_int64),
+        ("r", ctypes.c_double),
+        ("dt_dx", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("tile_width", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
+    ]
+
+
+class SweptError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libswept.so and declare its signatures. Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libswept.so not found at {path}; build it with "
+                           "`python -m paper_1811_08282_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    P = ctypes.POINTER(sw_problem)
+    sig = {
+        "sw_create": ([P, ctypes.POINTER(vp)], ctypes.c_int),
+        "sw_destroy": ([vp], None),
+        "sw_state_planes": ([P], ctypes.c_int),
+        "sw_state_bytes": ([P], i64),
+        "sw_run": ([vp, vp, i64, vp], ctypes.c_int),
+        "sw_run_host": ([vp, vp, vp, i64, vp], ctypes.c_int),
+        "sw_pack_fp64": ([P, vp, vp, vp], ctypes.c_int),
+        "sw_unpack_fp64": ([P, vp, vp, vp], ctypes.c_int),
+        "sw_conservation": ([vp, vp, ctypes.POINTER(dbl), vp], ctypes.c_int),
+        "sw_check_physical": ([vp, vp, ctypes.POINTER(i64), vp], ctypes.c_int),
+        "sw_sync_status": ([vp, vp], ctypes.c_int),
+        "sw_last_launch_count": ([vp], i64),
+        "sw_tile_width": ([vp], i32),
+        "sw_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "sw_abi_version": ([], ctypes.c_int),
+        "sw_set_timing": ([vp, i64], ctypes.c_int),
+        "sw_launch_times": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32), i64], i64),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load().sw_status_string(int(code)).decode()
+
+
+def _ptr(x) -> int:
+    """Device (or host) address of a torch tensor, or an int passed through."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        raise SweptError(rc, where)
+    return rc
+
+
+@dataclass
+class Problem:
+    """Python view of ``sw_problem`` (Section 3.2's problem statement)."""
+    scheme: int = SW_HEAT
+    precision: int = SW_FP64
+    boundary: int = SW_PERIODIC
+    method: int = SW_SWEPT
+    n: int = 1024
+    r: float = 0.25
+    dt_dx: float = 0.0
+    gamma: float = 1.4
+    tile_width: int = 0
+    flags: int = 0
+
+    def c(self) -> sw_problem:
+        return sw_problem(int(self.scheme), int(self.precision), int(self.boundary), int(self.method),
+                          int(self.n), float(self.r), float(self.dt_dx), float(self.gamma),
+                          int(self.tile_width), int(self.flags))
+
+    @property
+    def nv(self) -> int:
+        return 1 if self.scheme == SW_HEAT else 3
+
+
+def sw_state_planes(p: Problem) -> int:
+    return _check(load().sw_state_planes(ctypes.byref(p.c())), "sw_state_planes")
+
+
+def sw_state_bytes(p: Problem) -> int:
+    return _check(load().sw_state_bytes(ctypes.byref(p.c())), "sw_state_bytes")
+
+
+def sw_abi_version() -> int:
+    return load().sw_abi_version()
+
+
+def sw_status_string(code: int) -> str:
+    return status_string(code)
+
+
+def sw_pack_fp64(p: Problem, src_fp64, dst_state, stream=None) -> None:
+    _check(load().sw_pack_fp64(ctypes.byref(p.c()), _ptr(src_fp64), _ptr(dst_state), _stream(stream)),
+           "sw_pack_fp64")
+
+
+def sw_unpack_fp64(p: Problem, src_state, dst_fp64, stream=None) -> None:
+    _check(load().sw_unpack_fp64(ctypes.byref(p.c()), _ptr(src_state), _ptr(dst_fp64), _stream(stream)),
+           "sw_unpack_fp64")
+
+
+class Handle:
+    """Owner of an ``sw_handle`` (scratch on the current device)."""
+
+    def __init__(self, problem: Problem):
+        self.problem = problem
+        self._cp = problem.c()
+        h = ctypes.c_void_p()
+        rc = load().sw_create(ctypes.byref(self._cp), ctypes.byref(h))
+        _check(rc, "sw_create")
+        self.warning = rc
+        self._h = h
+
+    @property
+    def ptr(self) -> int:
+        return self._h.value
+
+    def close(self) -> None:
+        if self._h and self._h.value:
+            load().sw_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sw_run(self, state, nsteps: int, stream=None) -> None:
+        _check(load().sw_run(self._h, _ptr(state), int(nsteps), _stream(stream)), "sw_run")
+
+    def sw_run_host(self, state_in, state_out, nsteps: int, stream=None) -> None:
+        _check(load().sw_run_host(self._h, _ptr(state_in), _ptr(state_out), int(nsteps), _stream(stream)),
+               "sw_run_host")
+
+    def sw_conservation(self, state, stream=None):
+        sums = (ctypes.c_double * 3)()
+        _check(load().sw_conservation(self._h, _ptr(state), sums, _stream(stream)), "sw_conservation")
+        return [sums[i] for i in range(self.problem.nv)]
+
+    def sw_check_physical(self, state, stream=None) -> int:
+        """Returns -1 when every cell has rho > 0, p > 0 and finite values, else the first bad cell."""
+        cell = ctypes.c_int64(-1)
+        rc = load().sw_check_physical(self._h, _ptr(state), ctypes.byref(cell), _stream(stream))
+        if rc not in (SW_OK, SW_ERR_NONPHYSICAL):
+            _check(rc, "sw_check_physical")
+        return int(cell.value)
+
+    def sw_sync_status(self, stream=None) -> int:
+        return load().sw_sync_status(self._h, _stream(stream))
+
+    def sw_last_launch_count(self) -> int:
+        return int(load().sw_last_launch_count(self._h))
+
+    def sw_tile_width(self) -> int:
+        return int(load().sw_tile_width(self._h))
+
+    def sw_set_timing(self, capacity: int) -> None:
+        _check(load().sw_set_timing(self._h, int(capacity)), "sw_set_timing")
+
+    def sw_launch_times(self, cap: int = 1 << 16):
+        """[(ms, kind)] of the last run's traced launches (kind 0 Up, 1 Diamond, 2 Down, 3 per-step)."""
+        ms = (ctypes.c_float * cap)()
+        kind = (ctypes.c_int32 * cap)()
+        cnt = _check(int(load().sw_launch_times(self._h, ms, kind, int(cap))), "sw_launch_times")
+        return [(float(ms[i]), int(kind[i])) for i in range(cnt)]
+
+
+def sw_create(problem: Problem) -> Handle:
+    return Handle(problem)
+
+
+# --------------------------------------------------------------- conveniences
+def state_dtype(p: Problem):
+    import torch
+    return torch.float64 if p.precision == SW_FP64 else torch.float32
+
+
+def to_state(p: Problem, fp64_planes, stream=None):
+    """Device state in the working layout of ``p`` from FP64 planes (torch, cuda)."""
+    import torch
+    src = fp64_planes.to(device="cuda", dtype=torch.float64).contiguous()
+    assert src.numel() == p.nv * p.n
+    planes = sw_state_planes(p)
+    dst = torch.empty(planes * p.n, dtype=state_dtype(p), device="cuda")
+    sw_pack_fp64(p, src, dst, stream)
+    return dst
+
+
+def to_fp64(p: Problem, state, stream=None):
+    """FP64 planes (nv, n) on the device from a state in the working layout."""
+    import torch
+    out = torch.empty(p.nv * p.n, dtype=torch.float64, device="cuda")
+    sw_unpack_fp64(p, state, out, stream)
+    return out.view(p.nv, p.n)
+
+
+def run(p: Problem, fp64_planes, nsteps: int):
+    """One-call form: FP64 planes in (numpy or torch), FP64 planes (torch, cuda) out."""
+    import torch
+    x = torch.as_tensor(fp64_planes, dtype=torch.float64)
+    st = to_state(p, x.reshape(-1))
+    with Handle(p) as h:
+        h.sw_run(st, nsteps)
+        out = to_fp64(p, st)
+        rc = h.sw_sync_status()
+        _check(rc, "sw_run (device status)")
+    return out
