@@ -50,7 +50,9 @@ CASES = [
 def _init(kind, n, seed=0):
     if kind == "sod":
         return I.sod(n), I.sod_lambda()
-    return I.riemann_initial(I.riemann_segments(n, min(64, n // 8), seed)), I.riemann_lambda()
+    # segments of >= 128 cells: much narrower ones interact within a few dozen steps and can
+    # reach near-vacuum, where the scheme itself (oracle included) loses positivity
+    return I.riemann_initial(I.riemann_segments(n, max(2, min(64, n // 128)), seed)), I.riemann_lambda()
 
 
 @pytest.mark.parametrize("n,W,steps,bc,kind", CASES)

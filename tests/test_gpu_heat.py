@@ -61,7 +61,9 @@ def test_fp64_swept_equals_perstep_and_oracle(n, W, steps, bc, r):
     assert norm_rel(sw, ref[None]) <= TOL_FP64
 
 
-@pytest.mark.parametrize("prec,tol", [(S.SW_FP32, 2e-5), (S.SW_FP32_COMP, 1e-10)])
+# FP32_COMP keeps the state to ~2^-48 but each increment is still rounded to FP32, so
+# its error grows like eps32 * (sum of |increments|): ~1e-9 on these fast-decaying modes
+@pytest.mark.parametrize("prec,tol", [(S.SW_FP32, 2e-5), (S.SW_FP32_COMP, 1e-8)])
 @pytest.mark.parametrize("n,W,steps,bc,r", [CASES[2], CASES[4], CASES[7], CASES[8]])
 def test_fp32_variants_swept_equals_perstep(prec, tol, n, W, steps, bc, r):
     u0 = _init(n, seed=7)
