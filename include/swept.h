@@ -75,6 +75,9 @@ extern "C" {
 #define SW_ERR_TIMEOUT (-4)      /* a bounded device-side wait expired */
 #define SW_ERR_NONPHYSICAL (-5)  /* Euler: rho <= 0, p <= 0 or NaN found */
 #define SW_ERR_UNSUPPORTED (-6)
+#define SW_ERR_TOO_LARGE (-7)    /* sw_run_noalloc: needs more than SW_NOALLOC_SCRATCH_BYTES */
+
+#define SW_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 #define SW_MIN_TILE 4
 #define SW_MAX_TILE 1024
@@ -158,6 +161,28 @@ SW_API int64_t sw_launch_times(sw_handle *h, float *ms, int32_t *kind, int64_t c
 
 /* Tile width actually used by the handle (after defaults). */
 SW_API int32_t sw_tile_width(const sw_handle *h);
+
+/* sw_run without any device allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code running
+ * inside a framework whose memory pool owns the device (a direct cudaMalloc
+ * fails or escapes the pool's accounting) and latency-critical loops that
+ * allow no allocation after start-up (cudaMalloc/cudaFree may synchronise).
+ * It runs the same swept phases as sw_run (method must be SW_SWEPT), but the
+ * flank buffers live in one static device array of SW_NOALLOC_SCRATCH_BYTES
+ * (16 MiB) compiled into the library, which every GPU that loads the library
+ * holds until the process exits. The caller passes the state, as for sw_run.
+ * Scratch needed: 2 * round_up_256(K * (n/W + 1) * 2W * element_size) bytes,
+ * K = 1 (heat FP64/FP32), 2 (heat FP32_COMP), 7 (Euler FP64/FP32),
+ * 10 (Euler FP32_COMP); larger problems are rejected with SW_ERR_TOO_LARGE
+ * before any launch (e.g. heat FP64 at W = 1024 fits n up to ~512k cells).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. All calls share the array and it keeps the last
+ * call's contents (nothing in it needs to start at zero); calls that overlap
+ * on the GPU race on it and must be serialised by the caller.
+ * Errors: SW_ERR_BAD_ARG (as sw_create, or method != SW_SWEPT),
+ * SW_ERR_TOO_LARGE, SW_ERR_UNSUPPORTED, SW_ERR_CUDA. */
+SW_API int sw_run_noalloc(const sw_problem *p, void *state, int64_t nsteps, void *stream);
 
 SW_API const char *sw_status_string(int status);
 SW_API int sw_abi_version(void);

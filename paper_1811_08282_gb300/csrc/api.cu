@@ -347,6 +347,9 @@ const char *sw_status_string(int s) {
     case SW_ERR_TIMEOUT: return "device-side wait timed out";
     case SW_ERR_NONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or NaN)";
     case SW_ERR_UNSUPPORTED: return "unsupported configuration";
+    case SW_ERR_TOO_LARGE:
+        return "problem needs more flank scratch than the static no-allocation buffer holds "
+               "(SW_NOALLOC_SCRATCH_BYTES)";
     default: return "unknown status";
     }
 }

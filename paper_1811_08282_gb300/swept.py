@@ -22,6 +22,8 @@ SW_SWEPT, SW_PERSTEP = 0, 1
 SW_OK, SW_WARN_UNSTABLE = 0, 1
 SW_ERR_BAD_ARG, SW_ERR_CUDA, SW_ERR_OOM = -1, -2, -3
 SW_ERR_TIMEOUT, SW_ERR_NONPHYSICAL, SW_ERR_UNSUPPORTED = -4, -5, -6
+SW_ERR_TOO_LARGE = -7
+SW_NOALLOC_SCRATCH_BYTES = 16 << 20
 SW_MIN_TILE, SW_MAX_TILE = 4, 1024
 
 # every symbol declared in include/swept.h
@@ -29,7 +31,7 @@ EXPORTS = (
     "sw_create", "sw_destroy", "sw_state_planes", "sw_state_bytes", "sw_run", "sw_run_host",
     "sw_pack_fp64", "sw_unpack_fp64", "sw_conservation", "sw_check_physical", "sw_sync_status",
     "sw_last_launch_count", "sw_tile_width", "sw_status_string", "sw_abi_version",
-    "sw_set_timing", "sw_launch_times",
+    "sw_set_timing", "sw_launch_times", "sw_run_noalloc",
 )
 
 
@@ -86,6 +88,7 @@ def load(path: str = LIB_PATH):
         "sw_abi_version": ([], ctypes.c_int),
         "sw_set_timing": ([vp, i64], ctypes.c_int),
         "sw_launch_times": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32), i64], i64),
+        "sw_run_noalloc": ([P, vp, i64, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -171,6 +174,15 @@ def sw_pack_fp64(p: Problem, src_fp64, dst_state, stream=None) -> None:
 def sw_unpack_fp64(p: Problem, src_state, dst_fp64, stream=None) -> None:
     _check(load().sw_unpack_fp64(ctypes.byref(p.c()), _ptr(src_state), _ptr(dst_fp64), _stream(stream)),
            "sw_unpack_fp64")
+
+
+def sw_run_noalloc(p: Problem, state, nsteps: int, stream=None) -> None:
+    """Swept run with no device allocation (flank scratch in the library's static
+    16 MiB device array); for callers that cannot call cudaMalloc. Calls share the
+    array: do not overlap them on the GPU."""
+    cp = p.c()
+    _check(load().sw_run_noalloc(ctypes.byref(cp), _ptr(state), int(nsteps), _stream(stream)),
+           "sw_run_noalloc")
 
 
 class Handle:
