@@ -70,10 +70,14 @@ def initial_state():
     return modes, r, I.heat_initial(modes)
 
 
+# sources that define the swept-phase kernel (the traffic figure is void once they change)
+KERNEL_SOURCES = ("common.cuh", "schemes.cuh", "swept_phase.cuh")
+
+
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1811_08282_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

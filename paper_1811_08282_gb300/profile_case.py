@@ -1,0 +1,73 @@
+"""Run one configured case through the C ABI (for profilers and quick timing).
+
+    python -m paper_1811_08282_gb300.profile_case --scheme heat --precision fp64 \
+        --method swept --n 16777216 --steps 2048 --width 1024 [--repeat 1]
+
+Inputs are the seeded synthetic states of ``inputs`` (heat: 32 sine modes;
+Euler: Sod, or 64 random Riemann segments with --init riemann). Prints the
+CUDA-event time of the last repeat and the cell-update rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+from . import inputs as I
+from . import swept as S
+
+PREC = {"fp64": S.SW_FP64, "fp32": S.SW_FP32, "fp32_comp": S.SW_FP32_COMP}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--scheme", choices=("heat", "euler"), default="heat")
+    ap.add_argument("--precision", choices=tuple(PREC), default="fp64")
+    ap.add_argument("--method", choices=("swept", "perstep"), default="swept")
+    ap.add_argument("--boundary", choices=("periodic", "transmissive"), default=None)
+    ap.add_argument("--init", choices=("sod", "riemann"), default="sod")
+    ap.add_argument("--n", type=int, default=1 << 24)
+    ap.add_argument("--steps", type=int, default=2048)
+    ap.add_argument("--width", type=int, default=1024)
+    ap.add_argument("--r", type=float, default=0.3)
+    ap.add_argument("--repeat", type=int, default=1)
+    a = ap.parse_args(argv)
+
+    import torch
+    from . import build
+    build.build()
+    heat = a.scheme == "heat"
+    bc = a.boundary or ("periodic" if heat else "transmissive")
+    p = S.Problem(scheme=S.SW_HEAT if heat else S.SW_EULER, precision=PREC[a.precision],
+                  boundary=S.SW_PERIODIC if bc == "periodic" else S.SW_TRANSMISSIVE,
+                  method=S.SW_SWEPT if a.method == "swept" else S.SW_PERSTEP, n=a.n, r=a.r,
+                  dt_dx=(I.sod_lambda() if a.init == "sod" else I.riemann_lambda()), gamma=I.GAMMA,
+                  tile_width=a.width if a.method == "swept" else 0)
+    if heat:
+        x = I.heat_initial(I.heat_modes(a.n, 32, seed=1))
+    elif a.init == "sod":
+        x = I.sod(a.n)
+    else:
+        x = I.riemann_initial(I.riemann_segments(a.n, 64, 1))
+    st = S.to_state(p, torch.as_tensor(x.reshape(-1), device="cuda"))
+    fresh = st.clone()
+    t = None
+    with S.Handle(p) as h:
+        for _ in range(a.repeat):
+            st.copy_(fresh)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            h.sw_run(st, a.steps)
+            e1.record()
+            e1.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+        launches = h.sw_last_launch_count()
+        rc = h.sw_sync_status()
+    print(json.dumps({"scheme": a.scheme, "precision": a.precision, "method": a.method, "n": a.n,
+                      "steps": a.steps, "width": a.width, "launches": launches, "seconds": t,
+                      "gcell_updates_per_s": a.n * a.steps / t / 1e9, "status": rc}))
+    return 0 if rc == 0 else 1
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
