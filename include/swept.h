@@ -79,6 +79,10 @@ extern "C" {
 
 #define SW_NOALLOC_SCRATCH_BYTES (16u << 20)
 
+/* sw_problem.flags */
+#define SW_FLAG_GENERIC 1  /* swept: use the generic shared-memory phase kernel for every
+                              phase (no register-resident Diamond kernel); same results */
+
 #define SW_MIN_TILE 4
 #define SW_MAX_TILE 1024
 
@@ -95,7 +99,7 @@ typedef struct sw_problem {
     double gamma;       /* Euler: ratio of specific heats (> 1) */
     int32_t tile_width; /* swept base width W: even, SW_MIN_TILE..SW_MAX_TILE,
                            divides n; 0 selects the library default */
-    int32_t flags;      /* reserved, must be 0 */
+    int32_t flags;      /* 0 or SW_FLAG_GENERIC (sw_run_noalloc: must be 0) */
 } sw_problem;
 
 typedef struct sw_handle sw_handle;

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/swept.h"
+#include "fold.h"
 #include "perstep.cuh"
 #include "schemes.cuh"
 #include "swept_phase.cuh"
@@ -41,6 +42,7 @@ struct sw_handle {
     std::vector<cudaEvent_t> events;
     std::vector<int32_t> kinds;
     int64_t ev_cap = 0, ev_used = 0;
+    int sms = 152;  // streaming multiprocessors of the device
 };
 
 namespace {
@@ -63,7 +65,7 @@ int validate(const sw_problem *p) {
     if (p->precision < SW_FP64 || p->precision > SW_FP32_COMP) return SW_ERR_BAD_ARG;
     if (p->boundary != SW_PERIODIC && p->boundary != SW_TRANSMISSIVE) return SW_ERR_BAD_ARG;
     if (p->method != SW_SWEPT && p->method != SW_PERSTEP) return SW_ERR_BAD_ARG;
-    if (p->flags != 0) return SW_ERR_BAD_ARG;
+    if (p->flags & ~SW_FLAG_GENERIC) return SW_ERR_BAD_ARG;
     if (p->n < 4 || p->n > (int64_t(1) << 40)) return SW_ERR_BAD_ARG;
     if (p->scheme == SW_HEAT) {
         if (!(p->r > 0.0) || !(p->r < 1e6)) return SW_ERR_BAD_ARG;
@@ -135,6 +137,10 @@ int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st) {
     const int H = h->H, W = h->W;
     const int64_t P_last = (L + H - 1) / H;
     const bool periodic = h->prob.boundary == SW_PERIODIC;
+    // complete Diamond phases of periodic heat problems go to the register-resident kernel
+    const bool fold = std::is_same<typename P::Params, HeatParams>::value && periodic &&
+                      !(h->prob.flags & SW_FLAG_GENERIC) && fold_supported(h->prob.precision, W);
+    const int64_t fold_warps = int64_t(h->sms) * fold_warps_per_sm(h->prob.precision, W);
     int64_t launches = 0;
     for (int64_t p = 0; p <= P_last; ++p) {
         PhaseArgs<T> a{};
@@ -159,7 +165,13 @@ int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st) {
         if constexpr (std::is_same<typename P::Params, HeatParams>::value) prm = h->hp;
         else prm = h->ep;
         trace_begin(h, launches, p == 0 ? 0 : (p == P_last ? 2 : 1), st);
-        k_swept_phase<P><<<(unsigned)a.nstruct, h->threads, h->smem, st>>>(a, prm);
+        if (fold && p >= 1 && a.lower == H && a.upper == H - 1 && !a.write_lower && !a.write_upper) {
+            cudaError_t e = launch_fold(h->prob.precision, W, a.p, h->M, h->S, a.flank_in, a.flank_out, h->hp,
+                                        fold_warps, st);
+            if (e != cudaSuccess) return cuda_status(e);
+        } else {
+            k_swept_phase<P><<<(unsigned)a.nstruct, h->threads, h->smem, st>>>(a, prm);
+        }
         trace_end(h, launches, st);
         ++launches;
     }
@@ -372,6 +384,8 @@ int sw_create(const sw_problem *p, sw_handle **out) {
     if (!h) return SW_ERR_OOM;
     h->prob = *p;
     cudaGetDevice(&h->device);
+    if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || h->sms <= 0)
+        h->sms = 152;
     h->esize = elem_size(*p);
     h->nio = planes_of(*p);
     // scheme constants, rounded once on the host

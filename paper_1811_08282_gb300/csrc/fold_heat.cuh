@@ -1,0 +1,226 @@
+// fold_heat.cuh -- register-resident Diamond phase for the heat equation
+// (Section 3.1, Fig. 1c), periodic grids, complete diamonds only.
+//
+// One warp owns a chain of consecutive diamonds of one phase. A diamond's
+// lower half widens (2, 4, ..., W cells per level) and its upper half narrows
+// (W-2, ..., 2): on its own it keeps half the lanes idle. Here the warp runs
+// the upper half of diamond k and the lower half of diamond k+1 on the same
+// levels: with diamond k+1's window shifted by W/2 around the warp, the two
+// active regions are exact complements, so every lane updates a live cell on
+// every level. The W cells of the folded window live in registers, K = W/32
+// per lane; neighbours cross lanes by shuffle (cyclically), and the only cells
+// that differ from a plain cyclic FTCS update are the four next to the seam
+// between the two diamonds, whose outer inputs come from the previous phase's
+// flanks: those inputs are swapped in by a select on the owner lane before the
+// one update every cell gets. The level loop is unrolled by K so that every
+// such cell is a compile-time register slot; its owner lane is computed at
+// run time.
+//
+// Flanks are read and written in the same global layout as k_swept_phase, so
+// the two kernels mix freely within one run (the generic kernel does the Up
+// and Down triangles and any truncated phase), and the per-cell update is the
+// same function, so results are bitwise identical.
+#pragma once
+#include "schemes.cuh"
+#include "swept_phase.cuh"
+
+namespace sw {
+
+// Cell policies: value type, update and warp shuffle.
+struct FoldF32 {
+    using T = float;
+    using V = float;
+    static constexpr int NSNAP = 1;
+    static __device__ __forceinline__ V upd(const HeatParams &p, V a, V u, V b) {
+        return heat_update<OpsF>(p.rf, a, u, b);
+    }
+    static __device__ __forceinline__ V shfl(V x, int src) { return __shfl_sync(0xffffffffu, x, src); }
+    static __device__ __forceinline__ V zero() { return 0.f; }
+    static __device__ __forceinline__ V load(const T *p, int64_t plane, int64_t i) { return p[i]; }
+    static __device__ __forceinline__ void store(T *p, int64_t plane, int64_t i, V x) { p[i] = x; }
+};
+
+struct FoldF64 {
+    using T = double;
+    using V = double;
+    static constexpr int NSNAP = 1;
+    static __device__ __forceinline__ V upd(const HeatParams &p, V a, V u, V b) {
+        return heat_update<OpsD>(p.r, a, u, b);
+    }
+    static __device__ __forceinline__ V shfl(V x, int src) { return __shfl_sync(0xffffffffu, x, src); }
+    static __device__ __forceinline__ V zero() { return 0.0; }
+    static __device__ __forceinline__ V load(const T *p, int64_t plane, int64_t i) { return p[i]; }
+    static __device__ __forceinline__ void store(T *p, int64_t plane, int64_t i, V x) { p[i] = x; }
+};
+
+struct FoldComp {
+    using T = float;
+    using V = HL;
+    static constexpr int NSNAP = 2;  // flank planes: high parts, low parts
+    static __device__ __forceinline__ V upd(const HeatParams &p, V a, V u, V b) {
+        return heat_update_comp(p.rf, p.rf_lo, a, u, b);
+    }
+    static __device__ __forceinline__ V shfl(V x, int src) {
+        return HL{__shfl_sync(0xffffffffu, x.h, src), __shfl_sync(0xffffffffu, x.l, src)};
+    }
+    static __device__ __forceinline__ V zero() { return HL{0.f, 0.f}; }
+    static __device__ __forceinline__ V load(const T *p, int64_t plane, int64_t i) {
+        return HL{p[i], p[plane + i]};
+    }
+    static __device__ __forceinline__ void store(T *p, int64_t plane, int64_t i, V x) {
+        p[i] = x.h;
+        p[plane + i] = x.l;
+    }
+};
+
+template <class T> struct FoldArgs {
+    int p;                // phase parity (1 odd: seam centred, 2 even: tile centred)
+    int64_t tiles;        // M (periodic: structures per phase)
+    int64_t nstruct_max;  // structures per flank buffer (flank layout of k_swept_phase)
+    const T *flank_in;
+    T *flank_out;
+};
+
+template <int K, class C>
+__global__ void __launch_bounds__(128) k_heat_fold(FoldArgs<typename C::T> a, HeatParams prm) {
+    using T = typename C::T;
+    using V = typename C::V;
+    constexpr int W = 32 * K, H = W / 2;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t M = a.tiles;
+    const int64_t b0 = gw * M / nw, b1 = (gw + 1) * M / nw;
+    if (b0 >= b1) return;  // whole warp
+    const int64_t S = a.nstruct_max;
+    const int64_t plane = S * 2 * (int64_t)W;  // flank field stride (FoldComp: low parts)
+
+    V v[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = C::zero();
+    int shift = 0;  // lanes by which the finishing diamond's frame is rotated (0 or 16)
+
+    for (int64_t t = 0; t <= b1 - b0; ++t) {
+        const bool hasL = t < b1 - b0;  // a diamond starting its lower half
+        const bool hasU = t > 0;        // a diamond finishing its upper half
+        const int64_t bL = b0 + t, bU = bL - 1;
+        int64_t lb, rb;
+        if (a.p & 1) {
+            lb = (bL - 1 + M) % M;
+            rb = bL % M;
+        } else {
+            lb = bL % M;
+            rb = (bL + 1) % M;
+        }
+        const T *srcL = a.flank_in + flank_off<T>(S, W, 0, lb, 1);   // left neighbour's right flank
+        const T *srcR = a.flank_in + flank_off<T>(S, W, 0, rb, 0);   // right neighbour's left flank
+        T *dU0 = a.flank_out + flank_off<T>(S, W, 0, bU < 0 ? 0 : bU, 0);
+        T *dU1 = a.flank_out + flank_off<T>(S, W, 0, bU < 0 ? 0 : bU, 1);
+        T *dL0 = a.flank_out + flank_off<T>(S, W, 0, bL % S, 0);
+        T *dL1 = a.flank_out + flank_off<T>(S, W, 0, bL % S, 1);
+
+        // flank entries 2(i-1)+k arrive in chunks of 32 (16 levels), one per lane, double-buffered
+        V cL = C::zero(), cR = C::zero(), nL = C::zero(), nR = C::zero();
+        if (hasL) {
+            cL = C::load(srcL, plane, lane);
+            cR = C::load(srcR, plane, lane);
+            if (W > 32) {
+                nL = C::load(srcL, plane, 32 + lane);
+                nR = C::load(srcR, plane, 32 + lane);
+            }
+        }
+
+        for (int g = 0; g < H / K; ++g) {
+#pragma unroll
+            for (int u = 0; u < K; ++u) {
+                const int i = g * K + u + 1;  // level within the phase half, 1..H
+                const int e = i - 1;
+                if (hasL && (e & 15) == 0 && e > 0) {
+                    cL = nL;
+                    cR = nR;
+                    const int c = (e >> 4) + 1;
+                    if (32 * c < W) {
+                        nL = C::load(srcL, plane, 32 * c + lane);
+                        nR = C::load(srcR, plane, 32 * c + lane);
+                    }
+                }
+                const int eo = 2 * (e & 15);
+                const V fl0 = C::shfl(cL, eo), fl1 = C::shfl(cL, eo + 1);
+                const V fr0 = C::shfl(cR, eo), fr1 = C::shfl(cR, eo + 1);
+                const V left_in = C::shfl(v[K - 1], (lane + 31) & 31);
+                const V right_in = C::shfl(v[0], (lane + 1) & 31);
+
+                // The four cells next to the seam between the two diamonds take some inputs
+                // from the flanks instead of the registers (slots static, owner lanes not):
+                //   z = W-i  (slot K-1-u): left <- fl0, self <- fl1, right <- fr0 on the first level
+                //   z = W-i+1 (slot K-u):  left <- fl1
+                //   z = i-1  (slot u):     self <- fr0, right <- fr1, left <- fl1 on the first level
+                //   z = i-2  (slot u-1):   right <- fr0
+                const bool first = (u == 0) && (g == 0);  // i == 1
+                const int sA = K - 1 - u, sB = (K - u) % K, sC = u, sD = (u + K - 1) % K;
+                const bool pA = hasL && lane == ((31 - g + shift) & 31);
+                const bool pB = hasL && !first && lane == ((((u == 0) ? 32 : 31) - g + shift) & 31);
+                const bool pC = hasL && lane == ((g + shift) & 31);
+                const bool pD = hasL && !first && lane == ((((u == 0) ? g - 1 : g) + shift + 32) & 31);
+                V nv[K];
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    V a = (j == 0) ? left_in : v[j - 1];
+                    V c = v[j];
+                    V b = (j == K - 1) ? right_in : v[j + 1];
+                    if (j == sA) {
+                        a = pA ? fl0 : a;
+                        c = pA ? fl1 : c;
+                        if (first) b = pA ? fr0 : b;
+                    }
+                    if (j == sB) a = pB ? fl1 : a;
+                    if (j == sC) {
+                        c = pC ? fr0 : c;
+                        b = pC ? fr1 : b;
+                        if (first) a = pC ? fl1 : a;
+                    }
+                    if (j == sD) b = pD ? fr0 : b;
+                    nv[j] = C::upd(prm, a, c, b);
+                }
+#pragma unroll
+                for (int j = 0; j < K; ++j) v[j] = nv[j];
+
+                // flank entries of the finishing diamond at level F + i (j = i)
+                if (hasU && i <= H - 1) {
+                    {   // z = i  -> left flank [2i]
+                        const int s = (u + 1) % K, lz = g + (u + 1) / K;
+                        if (lane == ((lz + shift) & 31)) C::store(dU0, plane, 2 * i, v[s]);
+                    }
+                    {   // z = i + 1 -> left flank [2i + 1]
+                        const int s = (u + 2) % K, lz = g + (u + 2) / K;
+                        if (lane == ((lz + shift) & 31)) C::store(dU0, plane, 2 * i + 1, v[s]);
+                    }
+                    {   // z = W - 2 - i -> right flank [2i]
+                        const int q = K - 3 - u;
+                        const int s = (q % K + K) % K, lz = 31 - g + (q < 0 ? -1 : 0);
+                        if (lane == ((lz + shift + 32) & 31)) C::store(dU1, plane, 2 * i, v[s]);
+                    }
+                    {   // z = W - 1 - i -> right flank [2i + 1]
+                        const int q = K - 2 - u;
+                        const int s = (q % K + K) % K, lz = 31 - g + (q < 0 ? -1 : 0);
+                        if (lane == ((lz + shift + 32) & 31)) C::store(dU1, plane, 2 * i + 1, v[s]);
+                    }
+                }
+                // the starting diamond's full row (level F): its flank entries j = 0
+                if (hasL && i == H) {
+                    if (lane == ((16 + shift) & 31)) {
+                        C::store(dL0, plane, 0, v[0]);
+                        C::store(dL0, plane, 1, v[1 % K]);
+                    }
+                    if (lane == ((15 + shift) & 31)) {
+                        C::store(dL1, plane, 0, v[K - 2]);
+                        C::store(dL1, plane, 1, v[K - 1]);
+                    }
+                }
+            }
+        }
+        shift ^= 16;
+    }
+}
+
+}  // namespace sw

@@ -25,6 +25,7 @@ SW_ERR_TIMEOUT, SW_ERR_NONPHYSICAL, SW_ERR_UNSUPPORTED = -4, -5, -6
 SW_ERR_TOO_LARGE = -7
 SW_NOALLOC_SCRATCH_BYTES = 16 << 20
 SW_MIN_TILE, SW_MAX_TILE = 4, 1024
+SW_FLAG_GENERIC = 1
 
 # every symbol declared in include/swept.h
 EXPORTS = (

@@ -46,9 +46,9 @@ def _init(n, seed=0):
     return I.heat_initial(I.heat_modes(n, 8, seed=seed, kmax=min(64, n // 4)))
 
 
-def _prob(n, W, r, bc, method, prec=S.SW_FP64):
+def _prob(n, W, r, bc, method, prec=S.SW_FP64, flags=0):
     return S.Problem(scheme=S.SW_HEAT, precision=prec, boundary=bc, method=method, n=n, r=r,
-                     tile_width=W if method == S.SW_SWEPT else 0)
+                     tile_width=W if method == S.SW_SWEPT else 0, flags=flags)
 
 
 @pytest.mark.parametrize("n,W,steps,bc,r", CASES)
@@ -72,6 +72,28 @@ def test_fp32_variants_swept_equals_perstep(prec, tol, n, W, steps, bc, r):
     assert np.array_equal(sw, ps)
     ref = oracle.heat_run(u0, r, steps, oracle.PERIODIC if bc == S.SW_PERIODIC else oracle.TRANSMISSIVE)
     assert norm_rel(sw, ref[None]) <= tol
+
+
+@pytest.mark.parametrize("prec", [S.SW_FP64, S.SW_FP32, S.SW_FP32_COMP])
+@pytest.mark.parametrize("n,W,steps", [
+    (256, 128, 300),       # two diamonds per phase: one per warp
+    (1024, 128, 1000),
+    (4096, 256, 777),      # ragged last phases run on the generic kernel
+    (1 << 16, 512, 1500),
+    (1 << 15, 1024, 2100),
+    (2048, 1024, 513),
+    (3 * 1024, 1024, 1025),  # odd number of diamonds
+])
+def test_register_diamond_kernel_matches_generic_kernel(prec, n, W, steps):
+    # periodic heat at W = 32K uses the register-resident Diamond kernel for every complete
+    # Diamond phase; SW_FLAG_GENERIC forces the shared-memory kernel everywhere
+    u0 = _init(n, seed=W + steps)
+    fast = run_gpu(_prob(n, W, 0.33, S.SW_PERIODIC, S.SW_SWEPT, prec), u0[None], steps)
+    gen = run_gpu(_prob(n, W, 0.33, S.SW_PERIODIC, S.SW_SWEPT, prec, flags=S.SW_FLAG_GENERIC), u0[None], steps)
+    assert np.array_equal(fast, gen), f"max diff {np.max(np.abs(fast - gen))}"
+    if prec == S.SW_FP64:
+        ref = oracle.heat_run(u0, 0.33, steps)
+        assert norm_rel(fast, ref[None]) <= TOL_FP64
 
 
 def test_compensated_beats_plain_fp32_where_fp32_stagnates():
