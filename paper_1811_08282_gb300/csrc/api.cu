@@ -137,7 +137,8 @@ int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st) {
     const int H = h->H, W = h->W;
     const int64_t P_last = (L + H - 1) / H;
     const bool periodic = h->prob.boundary == SW_PERIODIC;
-    // complete Diamond phases of periodic heat problems go to the register-resident kernel
+    // periodic heat at W = 32K: every phase except a truncated upper half (which stores its
+    // row mid-way) runs on the register-resident kernel
     const bool fold = std::is_same<typename P::Params, HeatParams>::value && periodic &&
                       !(h->prob.flags & SW_FLAG_GENERIC) && fold_supported(h->prob.precision, W);
     const int64_t fold_warps = int64_t(h->sms) * fold_warps_per_sm(h->prob.precision, W);
@@ -165,9 +166,10 @@ int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st) {
         if constexpr (std::is_same<typename P::Params, HeatParams>::value) prm = h->hp;
         else prm = h->ep;
         trace_begin(h, launches, p == 0 ? 0 : (p == P_last ? 2 : 1), st);
-        if (fold && p >= 1 && a.lower == H && a.upper == H - 1 && !a.write_lower && !a.write_upper) {
-            cudaError_t e = launch_fold(h->prob.precision, W, a.p, h->M, h->S, a.flank_in, a.flank_out, h->hp,
-                                        fold_warps, st);
+        if (fold && !a.write_upper) {
+            FoldPhase ph{a.p, a.n, h->M, h->S, a.lower, a.upper, a.write_lower, a.write_upper,
+                         a.flank_in, a.flank_out, state};
+            cudaError_t e = launch_fold(h->prob.precision, W, ph, h->hp, fold_warps, st);
             if (e != cudaSuccess) return cuda_status(e);
         } else {
             k_swept_phase<P><<<(unsigned)a.nstruct, h->threads, h->smem, st>>>(a, prm);

@@ -11,21 +11,31 @@ bool fold_supported(int precision, int W) {
     return W == 128 || W == 256 || W == 512 || W == 1024;
 }
 
+// Measured on GB300 at N = 2^24 (diamond phases, 4-warp CTAs; multiples of 4 keep
+// the SMs evenly loaded): FP32 peaks at 24 warps/SM up to W = 512, 12 at W = 1024;
+// FP32 hi/lo at 24 (W = 128), 16 (256), 12 (512); FP64 at 8.
 int fold_warps_per_sm(int precision, int W) {
-    if (precision == SW_FP32) return W >= 1024 ? 8 : 16;
-    return W >= 512 ? 8 : 16;
+    if (precision == SW_FP32) return W >= 1024 ? 12 : 24;
+    if (precision == SW_FP32_COMP) return W <= 128 ? 24 : (W == 256 ? 16 : (W == 512 ? 12 : 8));
+    return 8;
 }
 
 template <int K, class C>
-static cudaError_t go(int p, int64_t M, int64_t S, const void *fin, void *fout, const HeatParams &prm,
-                      int64_t warps, cudaStream_t st) {
+static cudaError_t go(const FoldPhase &ph, const HeatParams &prm, int64_t warps, cudaStream_t st) {
     using T = typename C::T;
     FoldArgs<T> a{};
-    a.p = p;
-    a.tiles = M;
-    a.nstruct_max = S;
-    a.flank_in = reinterpret_cast<const T *>(fin);
-    a.flank_out = reinterpret_cast<T *>(fout);
+    a.p = ph.p;
+    a.n = ph.n;
+    a.tiles = ph.M;
+    a.nstruct_max = ph.S;
+    a.lower = ph.lower;
+    a.upper = ph.upper;
+    a.write_lower = ph.write_lower;
+    a.write_upper = ph.write_upper;
+    a.flank_in = reinterpret_cast<const T *>(ph.flank_in);
+    a.flank_out = reinterpret_cast<T *>(ph.flank_out);
+    a.state = reinterpret_cast<T *>(ph.state);
+    const int64_t M = ph.M;
     if (warps > M) warps = M;
     if (warps < 1) warps = 1;
     const int64_t blocks = (warps + 3) / 4;  // 4 warps per CTA
@@ -34,23 +44,22 @@ static cudaError_t go(int p, int64_t M, int64_t S, const void *fin, void *fout, 
 }
 
 template <class C>
-static cudaError_t by_width(int W, int p, int64_t M, int64_t S, const void *fin, void *fout,
-                            const HeatParams &prm, int64_t warps, cudaStream_t st) {
+static cudaError_t by_width(int W, const FoldPhase &ph, const HeatParams &prm, int64_t warps, cudaStream_t st) {
     switch (W) {
-    case 128: return go<4, C>(p, M, S, fin, fout, prm, warps, st);
-    case 256: return go<8, C>(p, M, S, fin, fout, prm, warps, st);
-    case 512: return go<16, C>(p, M, S, fin, fout, prm, warps, st);
-    case 1024: return go<32, C>(p, M, S, fin, fout, prm, warps, st);
+    case 128: return go<4, C>(ph, prm, warps, st);
+    case 256: return go<8, C>(ph, prm, warps, st);
+    case 512: return go<16, C>(ph, prm, warps, st);
+    case 1024: return go<32, C>(ph, prm, warps, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_fold(int precision, int W, int p, int64_t M, int64_t S, const void *flank_in,
-                        void *flank_out, const HeatParams &prm, int64_t warps, cudaStream_t st) {
+cudaError_t launch_fold(int precision, int W, const FoldPhase &ph, const HeatParams &prm, int64_t warps,
+                        cudaStream_t st) {
     switch (precision) {
-    case SW_FP64: return by_width<FoldF64>(W, p, M, S, flank_in, flank_out, prm, warps, st);
-    case SW_FP32: return by_width<FoldF32>(W, p, M, S, flank_in, flank_out, prm, warps, st);
-    default: return by_width<FoldComp>(W, p, M, S, flank_in, flank_out, prm, warps, st);
+    case SW_FP64: return by_width<FoldF64>(W, ph, prm, warps, st);
+    case SW_FP32: return by_width<FoldF32>(W, ph, prm, warps, st);
+    default: return by_width<FoldComp>(W, ph, prm, warps, st);
     }
 }
 

@@ -11,11 +11,21 @@ namespace sw {
 // (W = 32 K, K in {4, 8, 16, 32}).
 bool fold_supported(int precision, int W);
 
-// One complete Diamond phase (parity p: 1 seam centred, 2 tile centred) of a
-// periodic heat problem with M tiles; flanks in the k_swept_phase layout with
-// S structures per buffer. `warps` warps share the M diamonds in contiguous chains.
-cudaError_t launch_fold(int precision, int W, int p, int64_t M, int64_t S, const void *flank_in,
-                        void *flank_out, const HeatParams &prm, int64_t warps, cudaStream_t st);
+// One phase of a periodic heat problem with M tiles (p: 0 Up Triangle, 1 seam
+// centred, 2 tile centred), `lower` / `upper` levels in its two halves, storing
+// the Down Triangle's row when write_lower is set (write_upper must be 0).
+// Flanks in the k_swept_phase layout with S structures per buffer; `warps` warps
+// share the M structures in contiguous chains.
+struct FoldPhase {
+    int p;
+    int64_t n, M, S;
+    int lower, upper, write_lower, write_upper;
+    const void *flank_in;
+    void *flank_out;
+    void *state;
+};
+cudaError_t launch_fold(int precision, int W, const FoldPhase &ph, const HeatParams &prm, int64_t warps,
+                        cudaStream_t st);
 
 // Warps per SM the launcher aims for at this precision / width (register bound).
 int fold_warps_per_sm(int precision, int W);

@@ -74,12 +74,41 @@ struct FoldComp {
 };
 
 template <class T> struct FoldArgs {
-    int p;                // phase parity (1 odd: seam centred, 2 even: tile centred)
+    int p;                // 0: Up Triangle; 1: seam-centred phase (odd); 2: tile-centred (even)
+    int64_t n;            // cells
     int64_t tiles;        // M (periodic: structures per phase)
     int64_t nstruct_max;  // structures per flank buffer (flank layout of k_swept_phase)
+    int lower, upper;     // levels of the lower / upper halves in this phase
+    int write_lower;      // Down Triangle: the lower half ends at the run's last level; store its row
+    int write_upper;      // must be 0 (a truncated upper half runs on the generic phase kernel)
     const T *flank_in;
     T *flank_out;
+    T *state;             // state planes (FoldComp: high plane, then low plane)
 };
+
+// Store the cells of one structure that the folded window holds at z in [zlo, zhi]
+// (zlo may be negative: the range wraps), z = window position in the frame of the
+// structure, y = (z + yoff) mod W its cell relative to the window start `start`.
+template <int K, class C>
+__device__ __forceinline__ void fold_store_row(const typename C::V (&v)[K], int lane, int shift, int zlo, int zhi,
+                                               int yoff, int64_t start, int64_t n, typename C::T *state) {
+    constexpr int W = 32 * K;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int x = lane * K + j;
+        int z = x - shift * K;
+        if (z < 0) z += W;
+        const bool in = (zlo >= 0) ? (z >= zlo && z <= zhi) : (z >= zlo + W || z <= zhi);
+        if (in) {
+            int y = z + yoff;
+            if (y >= W) y -= W;
+            int64_t cell = start + y;
+            cell %= n;
+            if (cell < 0) cell += n;
+            C::store(state, n, cell, v[j]);
+        }
+    }
+}
 
 template <int K, class C>
 __global__ void __launch_bounds__(128) k_heat_fold(FoldArgs<typename C::T> a, HeatParams prm) {
@@ -94,16 +123,23 @@ __global__ void __launch_bounds__(128) k_heat_fold(FoldArgs<typename C::T> a, He
     if (b0 >= b1) return;  // whole warp
     const int64_t S = a.nstruct_max;
     const int64_t plane = S * 2 * (int64_t)W;  // flank field stride (FoldComp: low parts)
+    const bool up = a.p == 0;
+    const int imax = up ? a.upper : (a.lower > a.upper ? a.lower : a.upper);
 
     V v[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) v[j] = C::zero();
     int shift = 0;  // lanes by which the finishing diamond's frame is rotated (0 or 16)
 
+    // Up Triangle: no pairing (two full rows cannot share the window); the iteration
+    // t finishes structure t-1's upper half after loading its row. Diamonds and the
+    // Down Triangle: iteration t runs structure t-1's upper half with structure t's
+    // lower half.
     for (int64_t t = 0; t <= b1 - b0; ++t) {
-        const bool hasL = t < b1 - b0;  // a diamond starting its lower half
-        const bool hasU = t > 0;        // a diamond finishing its upper half
-        const int64_t bL = b0 + t, bU = bL - 1;
+        const bool hasL = !up && t < b1 - b0 && a.lower > 0;
+        const bool hasU = (up ? t < b1 - b0 : t > 0) && a.upper > 0;
+        const int64_t bL = b0 + t, bU = up ? bL : bL - 1;
+        if (up && !(t < b1 - b0)) break;
         int64_t lb, rb;
         if (a.p & 1) {
             lb = (bL - 1 + M) % M;
@@ -112,12 +148,29 @@ __global__ void __launch_bounds__(128) k_heat_fold(FoldArgs<typename C::T> a, He
             lb = bL % M;
             rb = (bL + 1) % M;
         }
-        const T *srcL = a.flank_in + flank_off<T>(S, W, 0, lb, 1);   // left neighbour's right flank
-        const T *srcR = a.flank_in + flank_off<T>(S, W, 0, rb, 0);   // right neighbour's left flank
+        const T *srcL = a.flank_in + flank_off<T>(S, W, 0, hasL ? lb : 0, 1);  // left neighbour's right flank
+        const T *srcR = a.flank_in + flank_off<T>(S, W, 0, hasL ? rb : 0, 0);  // right neighbour's left flank
         T *dU0 = a.flank_out + flank_off<T>(S, W, 0, bU < 0 ? 0 : bU, 0);
         T *dU1 = a.flank_out + flank_off<T>(S, W, 0, bU < 0 ? 0 : bU, 1);
         T *dL0 = a.flank_out + flank_off<T>(S, W, 0, bL % S, 0);
         T *dL1 = a.flank_out + flank_off<T>(S, W, 0, bL % S, 1);
+        // window start (cell of relative position 0) of the starting structure
+        const int64_t startL = (a.p & 1) ? bL * W - H : bL * W;
+
+        if (up) {
+            // the initial row of tile bU, relative cell y at window position z = y (shift 0)
+            const int64_t base = bU * W + (int64_t)lane * K;
+#pragma unroll
+            for (int j = 0; j < K; ++j) v[j] = C::load(a.state, a.n, base + j);
+            if (lane == 0) {
+                C::store(dU0, plane, 0, v[0]);
+                C::store(dU0, plane, 1, v[1]);
+            }
+            if (lane == 31) {
+                C::store(dU1, plane, 0, v[K - 2]);
+                C::store(dU1, plane, 1, v[K - 1]);
+            }
+        }
 
         // flank entries 2(i-1)+k arrive in chunks of 32 (16 levels), one per lane, double-buffered
         V cL = C::zero(), cR = C::zero(), nL = C::zero(), nR = C::zero();
@@ -130,12 +183,15 @@ __global__ void __launch_bounds__(128) k_heat_fold(FoldArgs<typename C::T> a, He
             }
         }
 
-        for (int g = 0; g < H / K; ++g) {
+        for (int g = 0; g * K < imax; ++g) {
 #pragma unroll
             for (int u = 0; u < K; ++u) {
                 const int i = g * K + u + 1;  // level within the phase half, 1..H
+                if (i > imax) break;
+                const bool Lact = hasL && i <= a.lower;
+                const bool Uact = hasU && i <= a.upper;
                 const int e = i - 1;
-                if (hasL && (e & 15) == 0 && e > 0) {
+                if (Lact && (e & 15) == 0 && e > 0) {
                     cL = nL;
                     cR = nR;
                     const int c = (e >> 4) + 1;
@@ -158,35 +214,35 @@ __global__ void __launch_bounds__(128) k_heat_fold(FoldArgs<typename C::T> a, He
                 //   z = i-2  (slot u-1):   right <- fr0
                 const bool first = (u == 0) && (g == 0);  // i == 1
                 const int sA = K - 1 - u, sB = (K - u) % K, sC = u, sD = (u + K - 1) % K;
-                const bool pA = hasL && lane == ((31 - g + shift) & 31);
-                const bool pB = hasL && !first && lane == ((((u == 0) ? 32 : 31) - g + shift) & 31);
-                const bool pC = hasL && lane == ((g + shift) & 31);
-                const bool pD = hasL && !first && lane == ((((u == 0) ? g - 1 : g) + shift + 32) & 31);
+                const bool pA = Lact && lane == ((31 - g + shift) & 31);
+                const bool pB = Lact && !first && lane == ((((u == 0) ? 32 : 31) - g + shift) & 31);
+                const bool pC = Lact && lane == ((g + shift) & 31);
+                const bool pD = Lact && !first && lane == ((((u == 0) ? g - 1 : g) + shift + 32) & 31);
                 V nv[K];
 #pragma unroll
                 for (int j = 0; j < K; ++j) {
-                    V a = (j == 0) ? left_in : v[j - 1];
+                    V x = (j == 0) ? left_in : v[j - 1];
                     V c = v[j];
-                    V b = (j == K - 1) ? right_in : v[j + 1];
+                    V y = (j == K - 1) ? right_in : v[j + 1];
                     if (j == sA) {
-                        a = pA ? fl0 : a;
+                        x = pA ? fl0 : x;
                         c = pA ? fl1 : c;
-                        if (first) b = pA ? fr0 : b;
+                        if (first) y = pA ? fr0 : y;
                     }
-                    if (j == sB) a = pB ? fl1 : a;
+                    if (j == sB) x = pB ? fl1 : x;
                     if (j == sC) {
                         c = pC ? fr0 : c;
-                        b = pC ? fr1 : b;
-                        if (first) a = pC ? fl1 : a;
+                        y = pC ? fr1 : y;
+                        if (first) x = pC ? fl1 : x;
                     }
-                    if (j == sD) b = pD ? fr0 : b;
-                    nv[j] = C::upd(prm, a, c, b);
+                    if (j == sD) y = pD ? fr0 : y;
+                    nv[j] = C::upd(prm, x, c, y);
                 }
 #pragma unroll
                 for (int j = 0; j < K; ++j) v[j] = nv[j];
 
                 // flank entries of the finishing diamond at level F + i (j = i)
-                if (hasU && i <= H - 1) {
+                if (Uact && i <= H - 1) {
                     {   // z = i  -> left flank [2i]
                         const int s = (u + 1) % K, lz = g + (u + 1) / K;
                         if (lane == ((lz + shift) & 31)) C::store(dU0, plane, 2 * i, v[s]);
@@ -207,7 +263,7 @@ __global__ void __launch_bounds__(128) k_heat_fold(FoldArgs<typename C::T> a, He
                     }
                 }
                 // the starting diamond's full row (level F): its flank entries j = 0
-                if (hasL && i == H) {
+                if (Lact && i == H && a.upper > 0) {
                     if (lane == ((16 + shift) & 31)) {
                         C::store(dL0, plane, 0, v[0]);
                         C::store(dL0, plane, 1, v[1 % K]);
@@ -219,7 +275,9 @@ __global__ void __launch_bounds__(128) k_heat_fold(FoldArgs<typename C::T> a, He
                 }
             }
         }
-        shift ^= 16;
+        // Down Triangle: the lower half ends at the run's last level (the loop's last level)
+        if (a.write_lower && hasL) fold_store_row<K, C>(v, lane, shift, -a.lower, a.lower - 1, H, startL, a.n, a.state);
+        if (!up) shift ^= 16;
     }
 }
 

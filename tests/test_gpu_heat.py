@@ -83,6 +83,12 @@ def test_fp32_variants_swept_equals_perstep(prec, tol, n, W, steps, bc, r):
     (1 << 15, 1024, 2100),
     (2048, 1024, 513),
     (3 * 1024, 1024, 1025),  # odd number of diamonds
+    (4096, 256, 1),          # shorter than one Up Triangle
+    (4096, 256, 127),        # W/2 - 1: Up truncated, Down
+    (4096, 256, 128),        # exactly one Up + Down
+    (4096, 256, 129),
+    (4096, 256, 640),        # a multiple of W/2: complete Down Triangle
+    (8192, 512, 256 * 7 + 5),
 ])
 def test_register_diamond_kernel_matches_generic_kernel(prec, n, W, steps):
     # periodic heat at W = 32K uses the register-resident Diamond kernel for every complete
