@@ -70,21 +70,24 @@ def initial_state():
     return modes, r, I.heat_initial(modes)
 
 
-# sources that define the swept-phase kernel (the traffic figure is void once they change)
-KERNEL_SOURCES = ("common.cuh", "schemes.cuh", "swept_phase.cuh")
+# sources that define each timed kernel (a recorded traffic figure is void once they change)
+KERNEL_SOURCES = {
+    "k_heat_fold": ("common.cuh", "schemes.cuh", "swept_phase.cuh", "fold_heat.cuh"),
+    "k_swept_phase": ("common.cuh", "schemes.cuh", "swept_phase.cuh"),
+}
 
 
-def kernel_source_sha() -> str:
+def kernel_source_sha(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1811_08282_gb300", "csrc")
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernels are unchanged."""
+def recorded_traffic(kernel: str, key: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -95,9 +98,9 @@ def recorded_traffic(kernel: str):
             continue
         k, v = line.split("=", 1)
         vals[k.strip()] = v.strip()
-    if vals.get("source_sha") != kernel_source_sha() or f"{kernel}.bytes_per_launch" not in vals:
+    if vals.get(f"{kernel}.source_sha") != kernel_source_sha(kernel) or f"{key}.bytes_per_launch" not in vals:
         return None
-    return float(vals[f"{kernel}.bytes_per_launch"])
+    return float(vals[f"{key}.bytes_per_launch"])
 
 
 # ------------------------------------------------------------------ clocks
@@ -248,10 +251,16 @@ def run_ours(args):
     H = best_w // 2
     flops_per_launch = N * H * FLOPS_PER_UPDATE
     achieved = flops_per_launch / (statistics.mean(diamonds) / 1e3) / 1e12 if diamonds else None
-    traffic = recorded_traffic("k_swept_phase_heat_fp64")
+    # periodic heat at W = 32K runs its Diamonds on the register-resident kernel; the DRAM
+    # traffic of one Diamond launch is the flanks in and out (W-independent: 4 N values)
+    fold = best_w in (128, 256, 512, 1024)
+    kname = "k_heat_fold" if fold else "k_swept_phase"
+    traffic = recorded_traffic(kname, f"{kname}.heat_fp64.n2^24")
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": traffic,
-                "kernel": "k_swept_phase<HeatPolicy<FP64>> (Diamond)", "launches_traced": len(diamonds),
+                "kernel": (f"k_heat_fold<{best_w // 32}, FoldF64> (Diamond phases)" if fold
+                           else "k_swept_phase<HeatPolicy<FP64>> (Diamond phases)"),
+                "launches_traced": len(diamonds),
                 "avg_launch_ms": statistics.mean(diamonds) if diamonds else None,
                 "flops_per_launch": flops_per_launch,
                 "peak_source": "FP64 1.25 TFLOP/s class: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz (nominal, recipe)"}
@@ -277,12 +286,25 @@ def run_ours(args):
     compare = {}
     outputs = {("fp64", "swept", STEPS): final.cpu()}
     for name, prec in (("fp64", S.SW_FP64), ("fp32", S.SW_FP32), ("fp32_comp", S.SW_FP32_COMP)):
+        if name == "fp64":
+            w_prec = best_w
+        else:  # the same short timed sweep as for FP64
+            rates = {}
+            for W in WIDTHS[2:]:
+                pw = problem(prec, S.SW_SWEPT, W)
+                st = S.to_state(pw, u0_dev)
+                fresh = st.clone()
+                with S.Handle(pw) as hw:
+                    timed_run(hw, st, 64, fresh)
+                    rates[W] = TUNE_STEPS / timed_run(hw, st, TUNE_STEPS, fresh)
+                del st, fresh
+            w_prec = max(rates, key=rates.get)
         for method in ("swept", "perstep"):
             if name == "fp64" and method == "swept":
                 compare["fp64_swept"] = {"value": value / world, "steps": STEPS, "W": best_w}
                 continue
             steps = STEPS if method == "swept" else 5000
-            W = best_w if name == "fp64" else 1024
+            W = w_prec
             pp = problem(prec, S.SW_SWEPT if method == "swept" else S.SW_PERSTEP, W)
             st = S.to_state(pp, u0_dev)
             fresh = st.clone()
