@@ -188,6 +188,49 @@ SW_API int32_t sw_tile_width(const sw_handle *h);
  * SW_ERR_TOO_LARGE, SW_ERR_UNSUPPORTED, SW_ERR_CUDA. */
 SW_API int sw_run_noalloc(const sw_problem *p, void *state, int64_t nsteps, void *stream);
 
+/* ---- batches: many independent problems in one persistent launch ------------
+ * (Section 5 of the paper tunes the block size per problem; the batched launch
+ * and its device-side work queue are this library's addition.)
+ * sw_batch_create: `count` problems (all of one precision, method SW_SWEPT,
+ * flags 0, each with an explicit tile_width), problem i's device state at
+ * states[i] (layout as for sw_run, owned by the caller and used by every run),
+ * each advanced `nsteps` time steps per sw_batch_run. Allocates the flank
+ * buffers, per-structure completion flags and the work tables (owned by the
+ * batch). Errors: SW_ERR_BAD_ARG, SW_ERR_OOM, SW_ERR_CUDA, SW_ERR_UNSUPPORTED. */
+typedef struct sw_batch sw_batch;
+SW_API int sw_batch_create(const sw_problem *probs, void *const *states, int32_t count, int64_t nsteps,
+                           sw_batch **out);
+
+/* Advance every problem of the batch by nsteps: one persistent kernel whose
+ * CTAs take (phase, problem, chunk of structures) items from a device-side
+ * counter and wait (bounded, ~1 s) for the two neighbouring structures of the
+ * previous phase. The reset of the counter/flags and the launch are captured in
+ * a CUDA graph on the first call and replayed on `stream` afterwards.
+ * Asynchronous; results are bitwise those of sw_run on each problem. */
+SW_API int sw_batch_run(sw_batch *b, void *stream);
+
+/* Synchronise `stream`; return the last run's device status (SW_OK, or
+ * SW_ERR_TIMEOUT if a dependency wait ran out and the launch was abandoned). */
+SW_API int sw_batch_status(sw_batch *b, void *stream);
+
+/* Work items per run (for reporting). */
+SW_API int64_t sw_batch_items(const sw_batch *b);
+
+/* Failure-injection hook for tests: set the dependency-wait budget in clock
+ * cycles and, if drop_publish != 0, make structure 0 of problem 0 never
+ * publish its first phase so that its neighbours' waits run out. */
+SW_API int sw_batch_debug(sw_batch *b, int64_t wait_budget_cycles, int32_t drop_publish);
+
+SW_API void sw_batch_destroy(sw_batch *b);
+
+/* Tile-width autotuner (Section 5: "tested over a limited number of time steps
+ * and tuned to the best result"): times `probe_steps` steps of a uniform state
+ * of the problem for each W in {32, ..., 1024} that divides n (with n >= 2W),
+ * using the problem's own flags (SW_FLAG_GENERIC tunes the generic kernel that
+ * batches use), and writes the fastest to inout->tile_width. Allocates a
+ * temporary state; synchronises `stream`. */
+SW_API int sw_autotune(sw_problem *inout, int64_t probe_steps, void *stream);
+
 SW_API const char *sw_status_string(int status);
 SW_API int sw_abi_version(void);
 

@@ -98,9 +98,7 @@ int swept_threads(int W) {
     return std::min(512, std::max(32, t));
 }
 
-template <class P> size_t swept_smem(int W) {
-    return (size_t(P::NROW) * (W + 2) + size_t(P::NSNAP) * 2 * W) * sizeof(typename P::T);
-}
+template <class P> size_t swept_smem(int W) { return swept_smem_elems<P>(W) * sizeof(typename P::T); }
 
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return SW_OK;

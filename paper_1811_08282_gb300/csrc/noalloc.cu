@@ -62,7 +62,7 @@ int run_phases(const sw_problem &prob, int W, void *scratch, void *state, int64_
     if (2 * buf_bytes > SW_NOALLOC_SCRATCH_BYTES) return SW_ERR_TOO_LARGE;
     T *flank[2] = {reinterpret_cast<T *>(scratch),
                    reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(scratch) + buf_bytes)};
-    const size_t smem = (size_t(P::NROW) * (W + 2) + size_t(P::NSNAP) * 2 * W) * sizeof(T);
+    const size_t smem = swept_smem_elems<P>(W) * sizeof(T);
     if (smem > 227 * 1024) return SW_ERR_UNSUPPORTED;
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k_swept_phase<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=

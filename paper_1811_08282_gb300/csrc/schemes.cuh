@@ -70,6 +70,8 @@ template <> struct HeatPolicy<0> {  // FP64
     using O = OpsD;
     static constexpr int NROW = 2, NSNAP = 1, NIO = 1;
     static constexpr bool INJECT_AHEAD = true;
+    static constexpr bool TWO_PASS = false;
+    static constexpr int NSCR = 0;
     using Params = HeatParams;
     static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
         row[s] = st[j];
@@ -101,6 +103,8 @@ template <> struct HeatPolicy<1> {  // FP32
     using O = OpsF;
     static constexpr int NROW = 2, NSNAP = 1, NIO = 1;
     static constexpr bool INJECT_AHEAD = true;
+    static constexpr bool TWO_PASS = false;
+    static constexpr int NSCR = 0;
     using Params = HeatParams;
     static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
         row[s] = st[j];
@@ -131,6 +135,8 @@ template <> struct HeatPolicy<2> {  // FP32 hi/lo compensated
     using T = float;
     static constexpr int NROW = 4, NSNAP = 2, NIO = 2;  // row: h0 l0 h1 l1; planes: hi, lo
     static constexpr bool INJECT_AHEAD = true;
+    static constexpr bool TWO_PASS = false;
+    static constexpr int NSCR = 0;
     using Params = HeatParams;
     static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
         row[s] = st[j];
@@ -254,6 +260,8 @@ template <int PREC> struct EulerPolicy {
     using T = typename O::T;
     static constexpr int NROW = 7, NSNAP = 7, NIO = 3;
     static constexpr bool INJECT_AHEAD = false;
+    static constexpr bool TWO_PASS = true;
+    static constexpr int NSCR = 3;  // face flux components (or the pressure) per position
     using Params = EulerParams;
     static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
         row[s] = st[j];
@@ -276,32 +284,52 @@ template <int PREC> struct EulerPolicy {
 #pragma unroll
         for (int f = 0; f < NSNAP; ++f) row[f * rs + s] = stg[f * ss + e];
     }
-    static __device__ __forceinline__ void step(const Params &prm, T *row, int rs, int s, int64_t level,
-                                                bool gl, bool gr) {
+    // Two passes per sub-step (the per-cell results are those of evaluating both
+    // faces and all three pressures per cell; each is computed once here):
+    // pre():  ratio sub-steps -> p at each position in [lo-1, hi+1];
+    //         flux sub-steps  -> the face flux between positions s-1 and s, s in [lo, hi+1].
+    // step(): the cell update from the scratch values.
+    // gl: cell s is the domain's first cell; gr_prev: cell s-1 is its last (transmissive).
+    static __device__ __forceinline__ void pre(const Params &prm, const T *row, int rs, T *scr, int s,
+                                               int64_t level, int lo, int hi, int slo, int shi, bool gl,
+                                               bool gr_prev) {
         const EulerK<O> k = eu_k<O>(prm);
         const int kind = (int)(level & 3);
-        const int sl = gl ? s : s - 1, sr = gr ? s : s + 1;
         if (kind == 0 || kind == 2) {
+            if (s < slo || s > shi) return;
             const T *q = row + (kind == 0 ? 0 : 3) * rs;
-            T pm = eu_pressure<O>(k, q[sl], q[rs + sl], q[2 * rs + sl]);
-            T p0 = eu_pressure<O>(k, q[s], q[rs + s], q[2 * rs + s]);
-            T pp = eu_pressure<O>(k, q[sr], q[rs + sr], q[2 * rs + sr]);
-            row[6 * rs + s] = eu_ratio<O>(pm, p0, pp);
+            scr[s] = eu_pressure<O>(k, q[s], q[rs + s], q[2 * rs + s]);
         } else {
+            if (s < lo) return;
             const T *q = row + (kind == 1 ? 0 : 3) * rs;
             const T *th = row + 6 * rs;
-            T thl = gl ? T(0) : th[sl], th0 = th[s], thr = gr ? T(0) : th[sr];
-            T fa0, fa1, fa2, fb0, fb1, fb2;
-            eu_face_flux<O>(k, q[sl], q[rs + sl], q[2 * rs + sl], thl, q[s], q[rs + s], q[2 * rs + s], th0, fa0,
-                            fa1, fa2);
-            eu_face_flux<O>(k, q[s], q[rs + s], q[2 * rs + s], th0, q[sr], q[rs + sr], q[2 * rs + sr], thr, fb0,
-                            fb1, fb2);
+            int a = s - 1, b = s;
+            T tha, thb;
+            if (gl) { a = s; tha = T(0); thb = th[s]; }
+            else if (gr_prev) { b = s - 1; tha = th[s - 1]; thb = T(0); }
+            else { tha = th[s - 1]; thb = th[s]; }
+            T f0, f1, f2;
+            eu_face_flux<O>(k, q[a], q[rs + a], q[2 * rs + a], tha, q[b], q[rs + b], q[2 * rs + b], thb, f0, f1,
+                            f2);
+            scr[s] = f0;
+            scr[rs + s] = f1;
+            scr[2 * rs + s] = f2;
+        }
+    }
+    static __device__ __forceinline__ void step(const Params &prm, T *row, int rs, const T *scr, int s,
+                                                int64_t level, bool gl, bool gr) {
+        const EulerK<O> k = eu_k<O>(prm);
+        const int kind = (int)(level & 3);
+        if (kind == 0 || kind == 2) {
+            const T pm = gl ? scr[s] : scr[s - 1], pp = gr ? scr[s] : scr[s + 1];
+            row[6 * rs + s] = eu_ratio<O>(pm, scr[s], pp);
+        } else {
             const T c = (kind == 1) ? k.hlam : k.lam;
             T *out = row + (kind == 1 ? 3 : 0) * rs;
-            T q0 = row[s], q1 = row[rs + s], q2 = row[2 * rs + s];
-            out[s] = O::sub(q0, O::mul(c, O::sub(fb0, fa0)));
-            out[rs + s] = O::sub(q1, O::mul(c, O::sub(fb1, fa1)));
-            out[2 * rs + s] = O::sub(q2, O::mul(c, O::sub(fb2, fa2)));
+            const T q0 = row[s], q1 = row[rs + s], q2 = row[2 * rs + s];
+            out[s] = O::sub(q0, O::mul(c, O::sub(scr[s + 1], scr[s])));
+            out[rs + s] = O::sub(q1, O::mul(c, O::sub(scr[rs + s + 1], scr[rs + s])));
+            out[2 * rs + s] = O::sub(q2, O::mul(c, O::sub(scr[2 * rs + s + 1], scr[2 * rs + s])));
         }
     }
 };
@@ -314,6 +342,8 @@ struct EulerPolicyComp {
     using T = float;
     static constexpr int NROW = 10, NSNAP = 10, NIO = 6;
     static constexpr bool INJECT_AHEAD = false;
+    static constexpr bool TWO_PASS = true;
+    static constexpr int NSCR = 3;
     using Params = EulerParams;
     static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
 #pragma unroll
@@ -334,27 +364,44 @@ struct EulerPolicyComp {
 #pragma unroll
         for (int f = 0; f < NSNAP; ++f) row[f * rs + s] = stg[f * ss + e];
     }
-    static __device__ __forceinline__ void step(const Params &prm, T *row, int rs, int s, int64_t level,
-                                                bool gl, bool gr) {
+    // Two passes per sub-step, as in EulerPolicy; fluxes and pressures from the
+    // high parts (Q^n) or the plain FP32 Q*.
+    static __device__ __forceinline__ void pre(const Params &prm, const T *row, int rs, T *scr, int s,
+                                               int64_t level, int lo, int hi, int slo, int shi, bool gl,
+                                               bool gr_prev) {
         const EulerK<O> k = eu_k<O>(prm);
         const int kind = (int)(level & 3);
-        const int sl = gl ? s : s - 1, sr = gr ? s : s + 1;
         if (kind == 0 || kind == 2) {
+            if (s < slo || s > shi) return;
             const T *q = row + (kind == 0 ? 0 : 6) * rs;
-            T pm = eu_pressure<O>(k, q[sl], q[rs + sl], q[2 * rs + sl]);
-            T p0 = eu_pressure<O>(k, q[s], q[rs + s], q[2 * rs + s]);
-            T pp = eu_pressure<O>(k, q[sr], q[rs + sr], q[2 * rs + sr]);
-            row[9 * rs + s] = eu_ratio<O>(pm, p0, pp);
+            scr[s] = eu_pressure<O>(k, q[s], q[rs + s], q[2 * rs + s]);
         } else {
+            if (s < lo) return;
             const T *q = row + (kind == 1 ? 0 : 6) * rs;
             const T *th = row + 9 * rs;
-            T thl = gl ? T(0) : th[sl], th0 = th[s], thr = gr ? T(0) : th[sr];
-            T fa0, fa1, fa2, fb0, fb1, fb2;
-            eu_face_flux<O>(k, q[sl], q[rs + sl], q[2 * rs + sl], thl, q[s], q[rs + s], q[2 * rs + s], th0, fa0,
-                            fa1, fa2);
-            eu_face_flux<O>(k, q[s], q[rs + s], q[2 * rs + s], th0, q[sr], q[rs + sr], q[2 * rs + sr], thr, fb0,
-                            fb1, fb2);
-            T df[3] = {__fsub_rn(fb0, fa0), __fsub_rn(fb1, fa1), __fsub_rn(fb2, fa2)};
+            int a = s - 1, b = s;
+            T tha, thb;
+            if (gl) { a = s; tha = T(0); thb = th[s]; }
+            else if (gr_prev) { b = s - 1; tha = th[s - 1]; thb = T(0); }
+            else { tha = th[s - 1]; thb = th[s]; }
+            T f0, f1, f2;
+            eu_face_flux<O>(k, q[a], q[rs + a], q[2 * rs + a], tha, q[b], q[rs + b], q[2 * rs + b], thb, f0, f1,
+                            f2);
+            scr[s] = f0;
+            scr[rs + s] = f1;
+            scr[2 * rs + s] = f2;
+        }
+    }
+    static __device__ __forceinline__ void step(const Params &prm, T *row, int rs, const T *scr, int s,
+                                                int64_t level, bool gl, bool gr) {
+        const EulerK<O> k = eu_k<O>(prm);
+        const int kind = (int)(level & 3);
+        if (kind == 0 || kind == 2) {
+            const T pm = gl ? scr[s] : scr[s - 1], pp = gr ? scr[s] : scr[s + 1];
+            row[9 * rs + s] = eu_ratio<O>(pm, scr[s], pp);
+        } else {
+            const T df[3] = {__fsub_rn(scr[s + 1], scr[s]), __fsub_rn(scr[rs + s + 1], scr[rs + s]),
+                             __fsub_rn(scr[2 * rs + s + 1], scr[2 * rs + s])};
             if (kind == 1) {
 #pragma unroll
                 for (int v = 0; v < 3; ++v) {

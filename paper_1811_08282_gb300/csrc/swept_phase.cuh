@@ -48,17 +48,58 @@ __device__ __forceinline__ int64_t flank_off(int64_t S, int W, int f, int64_t b,
     return ((f * S + b) * 2 + side) * (int64_t)W;
 }
 
-template <class P>
-__global__ void __launch_bounds__(512) k_swept_phase(PhaseArgs<typename P::T> a, typename P::Params prm) {
+// Flank loads: plain within a launch sequence (the L1 is not reused across
+// launches); L2-only (ld.global.cg) inside a persistent kernel, where another CTA
+// may have rewritten a flank that this SM's L1 still holds from an earlier item.
+template <bool CG, class T> __device__ __forceinline__ T flank_ld(const T *p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+// Shared memory of one structure, in elements of P::T: the row (NROW fields of
+// W+2 positions), the flank stage (NSNAP fields of 2W) and, for two-pass
+// policies, per-position scratch (NSCR fields of W+2).
+template <class P> __host__ __device__ constexpr size_t swept_smem_elems(int W) {
+    return size_t(P::NROW) * (W + 2) + size_t(P::NSNAP) * 2 * W + size_t(P::NSCR) * (W + 2);
+}
+
+// One sub-step over row positions [lo, hi]: two-pass policies first compute
+// per-position intermediates on [lo-1, hi+1] into scratch, then update cells.
+template <class P, class GL, class GR, class AFTER>
+__device__ __forceinline__ void swept_level(const typename P::Params &prm, typename P::T *row, int rs,
+                                            typename P::T *scr, int64_t lev, int lo, int hi, int slo, int shi,
+                                            GL ghost_l, GR ghost_r, AFTER after) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if constexpr (P::TWO_PASS) {
+        for (int s = lo - 1 + tid; s <= hi + 1; s += nt)
+            P::pre(prm, row, rs, scr, s, lev, lo, hi, slo, shi, ghost_l(s), ghost_r(s - 1));
+        __syncthreads();
+        for (int s = lo + tid; s <= hi; s += nt) {
+            P::step(prm, row, rs, scr, s, lev, ghost_l(s), ghost_r(s));
+            after(s);
+        }
+    } else {
+        for (int s = lo + tid; s <= hi; s += nt) {
+            P::step(prm, row, rs, s, lev, ghost_l(s), ghost_r(s));
+            after(s);
+        }
+    }
+}
+
+// The work of one structure (triangle or diamond) `b` of one phase, done by one
+// CTA (all its threads must call it). smem: swept_smem_elems<P>(W) elements.
+template <class P, bool CG>
+__device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &a,
+                                                const typename P::Params &prm, int64_t b,
+                                                typename P::T *smem) {
     using T = typename P::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *row = reinterpret_cast<T *>(smem_raw);
+    T *row = smem;
     const int W = a.W, H = a.H;
     const int rs = W + 2;                 // row stride (positions 0..W+1)
     T *stage = row + P::NROW * rs;        // [NSNAP][2 sides][W]
     const int ss = 2 * W;                 // stage field stride
+    T *scr = stage + P::NSNAP * ss;       // [NSCR][W+2] (two-pass policies)
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int64_t b = blockIdx.x;
     const int64_t n = a.n;
     const int64_t c = (a.p & 1) ? b * W : b * W + H;
     const int64_t base = c - H - 1;       // cell of row position 0
@@ -104,11 +145,11 @@ __global__ void __launch_bounds__(512) k_swept_phase(PhaseArgs<typename P::T> a,
         for (int f = 0; f < P::NSNAP; ++f) {
             if (has_l) {
                 const T *src = a.flank_in + flank_off<T>(S, W, f, lb, 1);
-                for (int e = tid; e < W; e += nt) stage[f * ss + e] = src[e];
+                for (int e = tid; e < W; e += nt) stage[f * ss + e] = flank_ld<CG>(src + e);
             }
             if (has_r) {
                 const T *src = a.flank_in + flank_off<T>(S, W, f, rb, 0);
-                for (int e = tid; e < W; e += nt) stage[f * ss + W + e] = src[e];
+                for (int e = tid; e < W; e += nt) stage[f * ss + W + e] = flank_ld<CG>(src + e);
             }
         }
         __syncthreads();
@@ -136,8 +177,7 @@ __global__ void __launch_bounds__(512) k_swept_phase(PhaseArgs<typename P::T> a,
             if (lo < slo) lo = slo;
             if (hi > shi) hi = shi;
             const bool last = (i == a.lower);
-            for (int s = lo + tid; s <= hi; s += nt) {
-                P::step(prm, row, rs, s, lev, ghost_l(s), ghost_r(s));
+            swept_level<P>(prm, row, rs, scr, lev, lo, hi, slo, shi, ghost_l, ghost_r, [&](int s) {
                 if (i == H && a.upper > 0) {  // full level F reached: flank entries j = 0
                     if (s == 1) P::snap_out(row, rs, s, lev + 1, stage, ss, 0);
                     if (s == 2) P::snap_out(row, rs, s, lev + 1, stage, ss, 1);
@@ -145,7 +185,7 @@ __global__ void __launch_bounds__(512) k_swept_phase(PhaseArgs<typename P::T> a,
                     if (s == W) P::snap_out(row, rs, s, lev + 1, stage, ss, W + 1);
                 }
                 if (last && a.write_lower) P::store_state(row, rs, s, lev + 1, a.state, n, cell(s));
-            }
+            });
             if (P::INJECT_AHEAD && i < a.lower) inject(i + 1);
             __syncthreads();
         }
@@ -158,14 +198,13 @@ __global__ void __launch_bounds__(512) k_swept_phase(PhaseArgs<typename P::T> a,
         if (lo < slo) lo = slo;
         if (hi > shi) hi = shi;
         const bool last = (i == a.upper);
-        for (int s = lo + tid; s <= hi; s += nt) {
-            P::step(prm, row, rs, s, lev, ghost_l(s), ghost_r(s));
+        swept_level<P>(prm, row, rs, scr, lev, lo, hi, slo, shi, ghost_l, ghost_r, [&](int s) {
             if (s == 1 + i) P::snap_out(row, rs, s, lev + 1, stage, ss, 2 * i);
             if (s == 2 + i) P::snap_out(row, rs, s, lev + 1, stage, ss, 2 * i + 1);
             if (s == W - 1 - i) P::snap_out(row, rs, s, lev + 1, stage, ss, W + 2 * i);
             if (s == W - i) P::snap_out(row, rs, s, lev + 1, stage, ss, W + 2 * i + 1);
             if (last && a.write_upper) P::store_state(row, rs, s, lev + 1, a.state, n, cell(s));
-        }
+        });
         __syncthreads();
     }
 
@@ -181,6 +220,12 @@ __global__ void __launch_bounds__(512) k_swept_phase(PhaseArgs<typename P::T> a,
             }
         }
     }
+}
+
+template <class P>
+__global__ void __launch_bounds__(512) k_swept_phase(PhaseArgs<typename P::T> a, typename P::Params prm) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    swept_structure<P, false>(a, prm, (int64_t)blockIdx.x, reinterpret_cast<typename P::T *>(smem_raw));
 }
 
 }  // namespace sw

@@ -147,3 +147,34 @@ RIEMANN_MAX_SPEED = 5.0
 
 def riemann_lambda(cfl: float = 0.4) -> float:
     return cfl / RIEMANN_MAX_SPEED
+
+
+# ------------------------------------------------------------------------ batches
+@dataclass(frozen=True)
+class BatchItem:
+    """One problem of a batch: heat (periodic, r) or Euler (transmissive Riemann problem)."""
+    scheme: str        # "heat" or "euler"
+    n: int
+    r: float           # heat only
+    planes: np.ndarray  # FP64 initial state, shape (nv, n)
+
+
+def batch_problems(count: int, seed: int, lo_exp: float = 10.0, hi_exp: float = 18.0,
+                   multiple: int = 256):
+    """Lengths log-uniform in [2^lo_exp, 2^hi_exp] rounded to a multiple of `multiple`;
+    even indices heat (r ~ U[0.1, 0.45], 8 sine modes, k <= min(64, n/8)), odd indices
+    Euler (one Riemann problem per domain, interface at the middle, states as in
+    riemann_segments)."""
+    e = uniform(seed, count, lo_exp, hi_exp, stream=21)
+    ns = np.maximum(multiple, np.round(2.0 ** e / multiple).astype(np.int64) * multiple)
+    rs = uniform(seed, count, 0.1, 0.45, stream=22)
+    out = []
+    for i in range(count):
+        n = int(ns[i])
+        if i % 2 == 0:
+            modes = heat_modes(n, 8, seed=seed * 100003 + i, kmax=min(64, max(1, n // 8)))
+            out.append(BatchItem("heat", n, float(rs[i]), heat_initial(modes)[None]))
+        else:
+            seg = riemann_segments(n, 2, seed * 100003 + i)
+            out.append(BatchItem("euler", n, 0.0, riemann_initial(seg)))
+    return out

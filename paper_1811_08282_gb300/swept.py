@@ -33,6 +33,8 @@ EXPORTS = (
     "sw_pack_fp64", "sw_unpack_fp64", "sw_conservation", "sw_check_physical", "sw_sync_status",
     "sw_last_launch_count", "sw_tile_width", "sw_status_string", "sw_abi_version",
     "sw_set_timing", "sw_launch_times", "sw_run_noalloc",
+    "sw_batch_create", "sw_batch_run", "sw_batch_status", "sw_batch_items", "sw_batch_debug",
+    "sw_batch_destroy", "sw_autotune",
 )
 
 
@@ -90,6 +92,13 @@ def load(path: str = LIB_PATH):
         "sw_set_timing": ([vp, i64], ctypes.c_int),
         "sw_launch_times": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32), i64], i64),
         "sw_run_noalloc": ([P, vp, i64, vp], ctypes.c_int),
+        "sw_batch_create": ([P, ctypes.POINTER(vp), i32, i64, ctypes.POINTER(vp)], ctypes.c_int),
+        "sw_batch_run": ([vp, vp], ctypes.c_int),
+        "sw_batch_status": ([vp, vp], ctypes.c_int),
+        "sw_batch_items": ([vp], i64),
+        "sw_batch_debug": ([vp, i64, i32], ctypes.c_int),
+        "sw_batch_destroy": ([vp], None),
+        "sw_autotune": ([P, i64, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -261,6 +270,62 @@ class Handle:
 
 def sw_create(problem: Problem) -> Handle:
     return Handle(problem)
+
+
+class Batch:
+    """Owner of an ``sw_batch``: problems[i] advanced on the device state states[i]."""
+
+    def __init__(self, problems, states, nsteps: int):
+        arr = (sw_problem * len(problems))(*[p.c() for p in problems])
+        ptrs = (ctypes.c_void_p * len(states))(*[_ptr(s) for s in states])
+        b = ctypes.c_void_p()
+        _check(load().sw_batch_create(arr, ptrs, len(problems), int(nsteps), ctypes.byref(b)),
+               "sw_batch_create")
+        self._b = b
+        self.problems = list(problems)
+        self.states = list(states)  # keep the device buffers alive
+
+    def close(self) -> None:
+        if self._b and self._b.value:
+            load().sw_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sw_batch_run(self, stream=None) -> None:
+        _check(load().sw_batch_run(self._b, _stream(stream)), "sw_batch_run")
+
+    def sw_batch_status(self, stream=None) -> int:
+        return int(load().sw_batch_status(self._b, _stream(stream)))
+
+    def sw_batch_items(self) -> int:
+        return int(load().sw_batch_items(self._b))
+
+    def sw_batch_debug(self, wait_budget_cycles: int, drop_publish: bool) -> None:
+        _check(load().sw_batch_debug(self._b, int(wait_budget_cycles), 1 if drop_publish else 0),
+               "sw_batch_debug")
+
+
+def sw_batch_create(problems, states, nsteps: int) -> Batch:
+    return Batch(problems, states, nsteps)
+
+
+def sw_autotune(p: Problem, probe_steps: int, stream=None) -> int:
+    """Fastest tile width for ``p`` over short timed runs; also stored in ``p.tile_width``."""
+    cp = p.c()
+    _check(load().sw_autotune(ctypes.byref(cp), int(probe_steps), _stream(stream)), "sw_autotune")
+    p.tile_width = int(cp.tile_width)
+    return p.tile_width
 
 
 # --------------------------------------------------------------- conveniences
