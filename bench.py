@@ -156,6 +156,24 @@ class ClockSampler:
                 "power_w_max": max(r["power"] for r in rows)}
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(t_local: float, world: int, device=None) -> float:
+    """Slowest rank's time (every rank gets it); the identity on one rank."""
+    if world <= 1:
+        return float(t_local)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(units_per_rank: float, t_max: float, world: int) -> float:
+    """Whole-job Gcell-updates/s: every rank (an independent replica) advances the same
+    units; the job takes as long as its slowest rank."""
+    return world * units_per_rank / t_max / 1e9
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import numpy as np
@@ -238,12 +256,8 @@ def run_ours(args):
     traced = h.sw_launch_times()
     h.sw_set_timing(0)
     final = S.to_fp64(p, state)[0]
-    t_total = sum(times)
-    if world > 1:
-        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(tt.item())
-    value = world * N * STEPS * args.steps / t_total / 1e9
+    t_total = max_over_ranks(sum(times), world, dev)
+    value = whole_job_rate(N * STEPS * args.steps, t_total, world)
     ms_per_step = t_total / args.steps * 1e3
 
     # roofline of the dominant kernel (Diamond phases), from the traced launches
