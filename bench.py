@@ -4,8 +4,8 @@
 Workload (one bench step): the FTCS heat equation, FP64, periodic grid of
 N = 2^24 cells, r drawn U[0.1, 0.45] (seeded), initial state a sum of 32 seeded
 sine modes, advanced 50,000 time steps by the swept rule (Up Triangle, Diamonds,
-Down Triangle; Section 3.1) with the tile base width chosen by a short timed
-sweep over W in {32, ..., 1024} (the paper's advice in Section 5: tune over a
+Down Triangle; Section 4.1) with the tile base width chosen by a short timed
+sweep over W in {32, ..., 1024} (the paper's advice in Section 6: tune over a
 limited number of steps). One cell-update = one cell advanced one time step.
 
 Printed (rank 0, one JSON line): the swept value, the per-step ("Classic")
@@ -216,7 +216,7 @@ def run_ours(args):
         b.synchronize()
         return a.elapsed_time(b) / 1e3
 
-    # 1) tile width: short timed sweep (Section 5: tune over a limited number of steps)
+    # 1) tile width: short timed sweep (Section 6: tune over a limited number of steps)
     sweep = {}
     for W in WIDTHS:
         p = problem(S.SW_FP64, S.SW_SWEPT, W)

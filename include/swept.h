@@ -4,10 +4,10 @@
  *
  * Paper: Magee, Walker & Niemeyer, "Applying the swept rule for solving explicit
  * partial differential equations on heterogeneous computing systems".
- *   Section 3.1 / Fig. 1:  Up Triangle, Communication, Diamond, Down Triangle.
- *   Section 3.2:           the problem statement (grid size, block size, scheme)
+ *   Section 4.1 / Fig. 1:  Up Triangle, Communication, Diamond, Down Triangle.
+ *   Section 4.2:           the problem statement (grid size, block size, scheme)
  *                          and the two test equations.
- *   Section 3.3 / Fig. 2:  per-step ("Classic") decomposition, flattening and
+ *   Section 4.3 / Fig. 2:  per-step ("Classic") decomposition, flattening and
  *                          lengthening; the 7-value Euler state per point.
  *
  * Conventions for every entry point:
@@ -49,7 +49,7 @@ extern "C" {
 #define SW_API
 #endif
 
-/* schemes (Section 3.2) */
+/* schemes (Section 4.2) */
 #define SW_HEAT 0   /* FTCS heat equation, r = alpha dt / dx^2 */
 #define SW_EULER 1  /* 2nd-order finite volume Euler, pressure-ratio minmod limiter */
 
@@ -62,7 +62,7 @@ extern "C" {
 #define SW_PERIODIC 0
 #define SW_TRANSMISSIVE 1  /* zero-gradient: the ghost copies the end cell */
 
-/* decomposition (Section 3.1: Swept vs Classic) */
+/* decomposition (Section 4.1: Swept vs Classic) */
 #define SW_SWEPT 0    /* Up Triangle, Diamond x k, Down Triangle */
 #define SW_PERSTEP 1  /* one launch per step (Euler: per stage, the flattened form) */
 
@@ -86,7 +86,7 @@ extern "C" {
 #define SW_MIN_TILE 4
 #define SW_MAX_TILE 1024
 
-/* The problem statement of Section 3.2: grid size, scheme, dt/dx (as r for
+/* The problem statement of Section 4.2: grid size, scheme, dt/dx (as r for
  * heat, lambda = dt/dx for Euler), block (tile) base width. */
 typedef struct sw_problem {
     int32_t scheme;     /* SW_HEAT or SW_EULER */
@@ -120,7 +120,7 @@ SW_API int64_t sw_state_bytes(const sw_problem *p);
 
 /* Advance the state in place by `nsteps` full time steps (Euler: 4 sub-steps
  * each) on `stream`. `state` is a device pointer in the layout above. Swept:
- * one launch per phase (Up, each Diamond, Down; Section 3.1); per-step: one
+ * one launch per phase (Up, each Diamond, Down; Section 4.1); per-step: one
  * launch per step (heat) or per stage (Euler). nsteps == 0 is a no-op.
  * Errors: SW_ERR_BAD_ARG (NULL state, nsteps < 0), SW_ERR_CUDA (launch). */
 SW_API int sw_run(sw_handle *h, void *state, int64_t nsteps, void *stream);
@@ -189,7 +189,7 @@ SW_API int32_t sw_tile_width(const sw_handle *h);
 SW_API int sw_run_noalloc(const sw_problem *p, void *state, int64_t nsteps, void *stream);
 
 /* ---- batches: many independent problems in one persistent launch ------------
- * (Section 5 of the paper tunes the block size per problem; the batched launch
+ * (Section 6 of the paper tunes the block size per problem; the batched launch
  * and its device-side work queue are this library's addition.)
  * sw_batch_create: `count` problems (all of one precision, method SW_SWEPT,
  * flags 0, each with an explicit tile_width), problem i's device state at
@@ -223,8 +223,8 @@ SW_API int sw_batch_debug(sw_batch *b, int64_t wait_budget_cycles, int32_t drop_
 
 SW_API void sw_batch_destroy(sw_batch *b);
 
-/* Tile-width autotuner (Section 5: "tested over a limited number of time steps
- * and tuned to the best result"): times `probe_steps` steps of a uniform state
+/* Tile-width autotuner (Section 6 advises tuning the block size on a
+ * few short runs): times `probe_steps` steps of a uniform state
  * of the problem for each W in {32, ..., 1024} that divides n (with n >= 2W),
  * using the problem's own flags (SW_FLAG_GENERIC tunes the generic kernel that
  * batches use), and writes the fastest to inout->tile_width. Allocates a

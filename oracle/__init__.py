@@ -82,7 +82,7 @@ def num_threads() -> int:
 
 
 def heat_run(u0, r: float, nsteps: int, boundary: int = PERIODIC) -> np.ndarray:
-    """FTCS heat equation, naive stepping (Section 3.2). Returns a new array."""
+    """FTCS heat equation, naive stepping (Section 4.2). Returns a new array."""
     u = np.array(u0, dtype=np.float64, copy=True, order="C")
     rc = _load().orc_heat_run(u.size, float(r), int(boundary), int(nsteps), _dptr(u))
     if rc != 0:
@@ -105,7 +105,7 @@ def heat_modes(n: int, r: float, nsteps: int, amps, ks, idx=None) -> np.ndarray:
 
 def euler_run(q0, lam: float, gamma: float, nsteps: int,
               boundary: int = TRANSMISSIVE) -> np.ndarray:
-    """Second-order FV Euler scheme, naive two-stage stepping (Section 3.2-3.3).
+    """Second-order FV Euler scheme, naive two-stage stepping (Sections 4.2-4.3).
 
     ``q0`` has shape (3, n): density, momentum, total energy. Returns a new array.
     """

@@ -8,12 +8,12 @@
  * What is computed here is the plain definition of each scheme: a naive
  * time-step loop over the whole grid, evaluated from the old time level for
  * every cell, with no tiles, no swept phases and no reordering. The swept rule
- * (Section 3.1 of Magee, Walker & Niemeyer, "Applying the swept rule for solving
+ * (Section 4.1 of Magee, Walker & Niemeyer, "Applying the swept rule for solving
  * explicit partial differential equations on heterogeneous computing systems")
  * states that swept and classic decompositions use the same numerical method, so
  * this naive loop is the reference result for both.
  *
- * The paper names its schemes but does not print them (Section 3.2: FTCS heat
+ * The paper names its schemes but does not print them (Section 4.2: FTCS heat
  * equation; second-order finite-volume Euler scheme with a minmod limiter). The
  * readings written out below are the project's fixed definition of those
  * schemes; each function states which reading it follows.
@@ -53,7 +53,7 @@ int orc_num_threads(void)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Heat equation, FTCS (Section 3.2: first-order forward in time, central in
+/* Heat equation, FTCS (Section 4.2: first-order forward in time, central in
  * space). Reading: u_j <- u_j + r*((u_{j-1} + u_{j+1}) - 2 u_j), r = alpha dt/dx^2,
  * all cells from the old level. Periodic: indices wrap. Transmissive
  * (zero-gradient): the ghost beyond each end copies the end cell.            */
@@ -115,7 +115,7 @@ int orc_heat_modes(int64_t n, double r, int64_t nsteps, int nmodes,
 
 /* ------------------------------------------------------------------------ */
 /* Euler equations, second-order finite volume with a minmod limiter driven by
- * the pressure ratio (Section 3.2; Section 3.3 / Fig. 2: the state carries
+ * the pressure ratio (Section 4.2; Section 4.3 / Fig. 2: the state carries
  * Q = {rho, rho u, E} and a pressure ratio, a predictor stage assigns and a
  * final stage adds). Reading used here (fixed project definition):
  *   p = (gamma-1) (E - 1/2 m u),  u = m / rho

@@ -5,7 +5,7 @@
     bt.batch.sw_batch_run(); bt.batch.sw_batch_status()
 
 Tile widths come from the library's autotuner (sw_autotune: short timed runs per
-width, Section 5's advice) applied once per (scheme, power-of-two size class) and
+width, Section 6's advice) applied once per (scheme, power-of-two size class) and
 then fitted to each problem's length (largest tuned-or-smaller width that divides
 it). Heat problems are periodic, Euler problems transmissive Riemann problems.
 """

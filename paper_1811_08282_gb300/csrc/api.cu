@@ -1,6 +1,6 @@
 // api.cu -- C ABI of libswept.so (declared in include/swept.h): problem
 // validation, scratch ownership, the host-side phase planner of the swept rule
-// (Section 3.1) and the per-step loop (Section 3.3), plus conversion,
+// (Section 4.1) and the per-step loop (Section 4.3), plus conversion,
 // conservation and positivity utilities. All compute runs in the kernels of
 // swept_phase.cuh and perstep.cuh; this file only plans and launches.
 #include <cuda_runtime.h>
@@ -85,7 +85,7 @@ int validate(const sw_problem *p) {
 }
 
 // Default base width: the largest of 1024, 512, ..., 4 that divides n with at
-// least two tiles (Section 5 recommends large blocks, 768-1024).
+// least two tiles (Section 6 recommends large blocks, 768-1024).
 int default_width(const sw_problem &p) {
     for (int W = SW_MAX_TILE; W >= SW_MIN_TILE; W >>= 1)
         if (p.n % W == 0 && p.n >= 2 * (int64_t)W) return W;

@@ -4,7 +4,7 @@
 // Work items are (phase, problem, chunk of structures) in phase-major order; CTAs
 // take them from a device-side counter. An item of phase p waits (bounded spin)
 // until the structures of phase p-1 it depends on -- its left and right
-// neighbours, the same two as in Section 3.1's Communication step -- have
+// neighbours, the same two as in Section 4.1's Communication step -- have
 // published their phase, runs each structure with the same device code as the
 // per-phase kernel (so results equal sw_run's bitwise), and publishes. Items only
 // wait on items taken earlier, and a CTA only takes an item when it is running,

@@ -4,7 +4,7 @@
 // Every floating-point operation of the schemes goes through these wrappers so
 // that the compiler cannot contract a multiply and an add differently in two
 // kernels: the swept and the per-step kernels then evaluate the same rounded
-// sequence per cell and agree bitwise (Section 3.1: the swept rule uses the same
+// sequence per cell and agree bitwise (Section 4.1: the swept rule uses the same
 // numerical method as the classic decomposition).
 #pragma once
 #include <cstdint>

@@ -1,5 +1,5 @@
 // fold_heat.cuh -- register-resident Diamond phase for the heat equation
-// (Section 3.1, Fig. 1c), periodic grids, complete diamonds only.
+// (Section 4.1, Fig. 1c), periodic grids, complete diamonds only.
 //
 // One warp owns a chain of consecutive diamonds of one phase. A diamond's
 // lower half widens (2, 4, ..., W cells per level) and its upper half narrows

@@ -1,4 +1,4 @@
-// perstep.cuh -- the per-time-step ("Classic") kernels of Section 3.3 / Fig. 2a:
+// perstep.cuh -- the per-time-step ("Classic") kernels of Section 4.3 / Fig. 2a:
 // every launch reads the whole state from HBM and writes it back once.
 //
 // Heat: one launch per step, V consecutive cells per thread (vector loads),

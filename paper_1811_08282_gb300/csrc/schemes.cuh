@@ -1,4 +1,4 @@
-// schemes.cuh -- per-cell arithmetic of the two test equations (Section 3.2) and
+// schemes.cuh -- per-cell arithmetic of the two test equations (Section 4.2) and
 // the "policies" that tell the swept-phase driver how a cell is stored.
 //
 // Heat (FTCS): u' = u + r((u_{j-1} + u_{j+1}) - 2u), evaluated as
@@ -6,10 +6,10 @@
 // and as a hi/lo pair with an error-free state update (FP32_COMP).
 //
 // Euler (second-order finite volume, minmod limiter on the pressure ratio,
-// Rusanov flux, predictor + final stage; Section 3.2 and Fig. 2): evaluated in
+// Rusanov flux, predictor + final stage; Section 4.2 and Fig. 2): evaluated in
 // exactly the operation order of the scheme definition, no fused multiply-add,
 // IEEE division and square root, so FP64 results are reproducible bit for bit.
-// The lengthened sub-step cycle (Section 3.3, Fig. 2b; four 3-point sub-steps
+// The lengthened sub-step cycle (Section 4.3, Fig. 2b; four 3-point sub-steps
 // per time step) is, by sub-step index k = level % 4:
 //   k = 0: pressure ratio of Q^n            (stored in th)
 //   k = 1: predictor  Q* = Q^n - (lambda/2) (F_{i+1/2} - F_{i-1/2})(Q^n, th)
@@ -61,7 +61,7 @@ struct HeatParams {
 };
 
 // Storage policy for the swept driver. Row fields per position: two slots
-// (levels alternate between them, the "two values per point" of Section 3.1);
+// (levels alternate between them, the "two values per point" of Section 4.1);
 // a snapshot (flank entry) is the value at one level.
 template <int PREC> struct HeatPolicy;
 
@@ -251,9 +251,9 @@ template <> __device__ __forceinline__ EulerK<OpsF> eu_k<OpsF>(const EulerParams
 }
 
 // Row fields (FP64 / FP32): 0..2 Q^n, 3..5 Q*, 6 pressure ratio -- the seven values
-// per point of the lengthened state (Section 3.3). Updates are in place: a
+// per point of the lengthened state (Section 4.3). Updates are in place: a
 // sub-step reads one group of fields of its neighbours and writes another group
-// of its own, so no second buffer is needed (the alternation of Section 3.1).
+// of its own, so no second buffer is needed (the alternation of Section 4.1).
 template <int PREC> struct EulerPolicy {
     static_assert(PREC == 0 || PREC == 1, "plain Euler policy is FP64 or FP32");
     using O = typename std::conditional<PREC == 0, OpsD, OpsF>::type;

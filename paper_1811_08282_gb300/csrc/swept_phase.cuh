@@ -1,4 +1,4 @@
-// swept_phase.cuh -- one launch = one swept phase (Section 3.1, Fig. 1) over all
+// swept_phase.cuh -- one launch = one swept phase (Section 4.1, Fig. 1) over all
 // structures (triangles / diamonds) of that phase, one CTA per structure.
 //
 // Geometry (H = W/2, tiles [tW, tW+W), level = sub-step index):

@@ -5,10 +5,10 @@ no arithmetic of either numerical scheme: it only draws initial states and
 parameters (SplitMix64, a counter-based generator) and converts primitive gas
 states (rho, u, p) to the conservative variables the solvers take as input.
 
-Problem shapes follow Section 3.2 of the paper (1D heat equation and 1D Euler
-equations, grids of 2^10..2^24 points) and the synthetic recipe written in the
-design notes: sums of sine modes for heat; the Sod shock tube and seeded random
-Riemann problems for Euler.
+Problem shapes follow Section 4.2 of the paper (1D heat equation and 1D Euler
+equations, grids of powers of two): sums of seeded sine modes for heat; the Sod
+shock tube and seeded random Riemann problems for Euler; batches of both with
+log-uniform lengths.
 """
 from __future__ import annotations
 

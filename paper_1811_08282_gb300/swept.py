@@ -138,7 +138,7 @@ def _check(rc: int, where: str) -> int:
 
 @dataclass
 class Problem:
-    """Python view of ``sw_problem`` (Section 3.2's problem statement)."""
+    """Python view of ``sw_problem`` (Section 4.2's problem statement)."""
     scheme: int = SW_HEAT
     precision: int = SW_FP64
     boundary: int = SW_PERIODIC

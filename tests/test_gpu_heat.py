@@ -1,6 +1,6 @@
 """GPU parity of the FTCS heat path through the C ABI (swept phases and per-step kernel).
 
-- FP64 swept == FP64 per-step, bitwise (same per-cell arithmetic; Section 3.1 says
+- FP64 swept == FP64 per-step, bitwise (same per-cell arithmetic; Section 4.1 says
   the swept rule uses the same numerical method as the classic decomposition);
 - FP64 vs the FP64 oracle: norm-relative error <= 1e-12 (GPU uses fused
   multiply-adds, the oracle plain expressions; FTCS is a contraction for r <= 1/2,

@@ -1,4 +1,4 @@
-"""Pins of the Euler oracle and the exact Riemann solver (Section 3.2).
+"""Pins of the Euler oracle and the exact Riemann solver (Section 4.2).
 
 The paper names the scheme (second-order finite volume, minmod limiter, pressure
 ratio carried per point, predictor then final stage) without printing it; the

@@ -1,4 +1,4 @@
-"""Pins of the FTCS heat oracle (Section 3.2) to mathematics it cannot fake.
+"""Pins of the FTCS heat oracle (Section 4.2) to mathematics it cannot fake.
 
 - the dense matrix power (I + r L)^s u0 in extended precision (textbook linear algebra),
 - the exact discrete decay G(k)^s of Fourier modes, G(k) = 1 - 4 r sin^2(pi k/n),
