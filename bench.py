@@ -63,6 +63,11 @@ def dist_env():
         int(os.environ.get("WORLD_SIZE", "1"))
 
 
+def I_mod():
+    from paper_1811_08282_gb300 import inputs
+    return inputs
+
+
 def initial_state():
     from paper_1811_08282_gb300 import inputs as I
     modes = I.heat_modes(N, MODES, seed=SEED)
@@ -72,8 +77,8 @@ def initial_state():
 
 # sources that define each timed kernel (a recorded traffic figure is void once they change)
 KERNEL_SOURCES = {
-    "k_heat_fold": ("common.cuh", "schemes.cuh", "swept_phase.cuh", "fold_heat.cuh"),
-    "k_swept_phase": ("common.cuh", "schemes.cuh", "swept_phase.cuh"),
+    "k_heat_fold": ("common.cuh", "heat.cuh", "swept_phase.cuh", "fold_heat.cuh"),
+    "k_swept_phase": ("common.cuh", "heat.cuh", "swept_phase.cuh"),
 }
 
 
@@ -244,6 +249,7 @@ def run_ours(args):
     launches = 0
     barrier()
     sampler.start()
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed launches
     wall0 = time.perf_counter()
     for k in range(args.steps):
         if k == args.steps - 1:
@@ -252,6 +258,7 @@ def run_ours(args):
         launches += h.sw_last_launch_count()
     barrier()
     wall = time.perf_counter() - wall0
+    torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     traced = h.sw_launch_times()
     h.sw_set_timing(0)
@@ -329,6 +336,45 @@ def run_ours(args):
                                            "W": W if method == "swept" else None}
             outputs[(name, method, steps)] = S.to_fp64(pp, st)[0].cpu()
             del st, fresh
+    # small grid: the launch-latency-bound workload (N = 16384, r = 1/4, 8 modes, 1000 steps, W = 64)
+    small = {}
+    n_s, steps_s = 16384, 1000
+    u_s = torch.as_tensor(I_mod().heat_initial(I_mod().heat_modes(n_s, 8, seed=0)), device=dev)
+    for key, prec, method, W in (("fp64_swept_w64", S.SW_FP64, S.SW_SWEPT, 64),
+                                 ("fp64_perstep", S.SW_FP64, S.SW_PERSTEP, 0),
+                                 ("fp32_swept_w128", S.SW_FP32, S.SW_SWEPT, 128),
+                                 ("fp32_perstep", S.SW_FP32, S.SW_PERSTEP, 0)):
+        ps = S.Problem(scheme=S.SW_HEAT, precision=prec, boundary=S.SW_PERIODIC, method=method, n=n_s,
+                       r=0.25, tile_width=W)
+        st = S.to_state(ps, u_s)
+        fresh = st.clone()
+        with S.Handle(ps) as hs:
+            timed_run(hs, st, steps_s, fresh)
+            t = min(timed_run(hs, st, steps_s, fresh) for _ in range(5))
+            small[key] = {"ms": t * 1e3, "value": n_s * steps_s / t / 1e9, "launches": hs.sw_last_launch_count()}
+    small["speedup_fp64"] = small["fp64_perstep"]["ms"] / small["fp64_swept_w64"]["ms"]
+    small["speedup_fp32"] = small["fp32_perstep"]["ms"] / small["fp32_swept_w128"]["ms"]
+    compare["small_grid_n16384_1000_steps"] = small
+
+    # batched: 4096 independent problems (half heat, half Euler, lengths 2^10..2^18), FP32 hi/lo,
+    # autotuned widths, one persistent launch from a CUDA graph; a 200-step run
+    from paper_1811_08282_gb300 import batched
+    items = batched.default_items(4096, seed=7)
+    bt = batched.build(items, 200)
+    bt.batch.sw_batch_run()
+    bt.batch.sw_batch_status()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    bt.batch.sw_batch_run(stream)
+    b.record(stream)
+    b.synchronize()
+    tb = a.elapsed_time(b) / 1e3
+    compare["batched_4096"] = {"value": bt.cells * 200 / tb / 1e9, "unit": "Gcell-steps/s", "cells": bt.cells,
+                               "steps": 200, "ms": tb * 1e3, "items": bt.batch.sw_batch_items(),
+                               "status": bt.batch.sw_batch_status(), "precision": "fp32_comp"}
+    bt.batch.close()
+
     perstep_bytes = 16  # FP64 per-step: read + write one value per update
     compare["fp64_perstep"]["hbm_gbs"] = compare["fp64_perstep"]["value"] * perstep_bytes
     compare["speedup_swept_over_perstep_fp64"] = compare["fp64_swept"]["value"] / compare["fp64_perstep"]["value"]

@@ -3,7 +3,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "schemes.cuh"
+#include "heat.cuh"
 
 namespace sw {
 

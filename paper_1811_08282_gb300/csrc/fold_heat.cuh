@@ -21,7 +21,7 @@
 // and Down triangles and any truncated phase), and the per-cell update is the
 // same function, so results are bitwise identical.
 #pragma once
-#include "schemes.cuh"
+#include "heat.cuh"
 #include "swept_phase.cuh"
 
 namespace sw {

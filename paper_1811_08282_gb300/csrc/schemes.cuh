@@ -1,427 +1,5 @@
-// schemes.cuh -- per-cell arithmetic of the two test equations (Section 4.2) and
-// the "policies" that tell the swept-phase driver how a cell is stored.
-//
-// Heat (FTCS): u' = u + r((u_{j-1} + u_{j+1}) - 2u), evaluated as
-//   fma(r, fma(-2, u, a + b), u)                       (FP64, FP32)
-// and as a hi/lo pair with an error-free state update (FP32_COMP).
-//
-// Euler (second-order finite volume, minmod limiter on the pressure ratio,
-// Rusanov flux, predictor + final stage; Section 4.2 and Fig. 2): evaluated in
-// exactly the operation order of the scheme definition, no fused multiply-add,
-// IEEE division and square root, so FP64 results are reproducible bit for bit.
-// The lengthened sub-step cycle (Section 4.3, Fig. 2b; four 3-point sub-steps
-// per time step) is, by sub-step index k = level % 4:
-//   k = 0: pressure ratio of Q^n            (stored in th)
-//   k = 1: predictor  Q* = Q^n - (lambda/2) (F_{i+1/2} - F_{i-1/2})(Q^n, th)
-//   k = 2: pressure ratio of Q*
-//   k = 3: final      Q^{n+1} = Q^n - lambda (F_{i+1/2} - F_{i-1/2})(Q*, th*)
+// schemes.cuh -- the two test equations of Section 4.2: heat.cuh (FTCS) and
+// euler.cuh (second-order finite volume, pressure-ratio minmod limiter).
 #pragma once
-#include <type_traits>
-
-#include "common.cuh"
-
-namespace sw {
-
-// ============================================================================
-// Heat
-// ============================================================================
-template <class O>
-__device__ __forceinline__ typename O::T heat_update(typename O::T r, typename O::T a,
-                                                     typename O::T u, typename O::T b) {
-    using T = typename O::T;
-    return O::fma_(r, O::fma_(T(-2), u, O::add(a, b)), u);
-}
-
-struct HL {
-    float h, l;
-};
-
-// Compensated FTCS update of u = u.h + u.l (FP32 pair): the second difference is
-// formed from exactly-split differences of the high parts plus the low parts,
-// scaled by r = rh + rl, and added to the state with TwoSum so that increments
-// far below half an ulp of u are kept in the low part instead of rounding away.
-__device__ __forceinline__ HL heat_update_comp(float rh, float rl, HL a, HL u, HL b) {
-    float d1, e1, d2, e2;
-    two_sum(a.h, -u.h, d1, e1);
-    two_sum(b.h, -u.h, d2, e2);
-    float low = __fadd_rn(__fadd_rn(e1, e2), __fmaf_rn(-2.0f, u.l, __fadd_rn(a.l, b.l)));
-    float d = __fadd_rn(__fadd_rn(d1, d2), low);
-    float delta = __fmaf_rn(rh, d, __fmul_rn(rl, d));
-    float s, e;
-    two_sum(u.h, delta, s, e);
-    HL out;
-    fast_two_sum(s, __fadd_rn(u.l, e), out.h, out.l);
-    return out;
-}
-
-struct HeatParams {
-    double r;       // FP64 r
-    float rf;       // r rounded to float
-    float rf_lo;    // r - rf, rounded to float
-};
-
-// Storage policy for the swept driver. Row fields per position: two slots
-// (levels alternate between them, the "two values per point" of Section 4.1);
-// a snapshot (flank entry) is the value at one level.
-template <int PREC> struct HeatPolicy;
-
-template <> struct HeatPolicy<0> {  // FP64
-    using T = double;
-    using O = OpsD;
-    static constexpr int NROW = 2, NSNAP = 1, NIO = 1;
-    static constexpr bool INJECT_AHEAD = true;
-    static constexpr bool TWO_PASS = false;
-    static constexpr int NSCR = 0;
-    using Params = HeatParams;
-    static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
-        row[s] = st[j];
-    }
-    static __device__ __forceinline__ void store_state(const T *row, int rs, int s, int64_t level, T *st,
-                                                       int64_t n, int64_t j) {
-        st[j] = row[(level & 1) * rs + s];
-    }
-    static __device__ __forceinline__ void snap_out(const T *row, int rs, int s, int64_t level, T *stg, int ss,
-                                                    int e) {
-        stg[e] = row[(level & 1) * rs + s];
-    }
-    static __device__ __forceinline__ void snap_in(T *row, int rs, int s, int64_t level, const T *stg, int ss,
-                                                   int e) {
-        row[(level & 1) * rs + s] = stg[e];
-    }
-    static __device__ __forceinline__ void step(const Params &p, T *row, int rs, int s, int64_t level, bool gl,
-                                                bool gr) {
-        const T *cur = row + (level & 1) * rs;
-        T u = cur[s];
-        T a = gl ? u : cur[s - 1];
-        T b = gr ? u : cur[s + 1];
-        row[((level + 1) & 1) * rs + s] = heat_update<O>(p.r, a, u, b);
-    }
-};
-
-template <> struct HeatPolicy<1> {  // FP32
-    using T = float;
-    using O = OpsF;
-    static constexpr int NROW = 2, NSNAP = 1, NIO = 1;
-    static constexpr bool INJECT_AHEAD = true;
-    static constexpr bool TWO_PASS = false;
-    static constexpr int NSCR = 0;
-    using Params = HeatParams;
-    static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
-        row[s] = st[j];
-    }
-    static __device__ __forceinline__ void store_state(const T *row, int rs, int s, int64_t level, T *st,
-                                                       int64_t n, int64_t j) {
-        st[j] = row[(level & 1) * rs + s];
-    }
-    static __device__ __forceinline__ void snap_out(const T *row, int rs, int s, int64_t level, T *stg, int ss,
-                                                    int e) {
-        stg[e] = row[(level & 1) * rs + s];
-    }
-    static __device__ __forceinline__ void snap_in(T *row, int rs, int s, int64_t level, const T *stg, int ss,
-                                                   int e) {
-        row[(level & 1) * rs + s] = stg[e];
-    }
-    static __device__ __forceinline__ void step(const Params &p, T *row, int rs, int s, int64_t level, bool gl,
-                                                bool gr) {
-        const T *cur = row + (level & 1) * rs;
-        T u = cur[s];
-        T a = gl ? u : cur[s - 1];
-        T b = gr ? u : cur[s + 1];
-        row[((level + 1) & 1) * rs + s] = heat_update<O>(p.rf, a, u, b);
-    }
-};
-
-template <> struct HeatPolicy<2> {  // FP32 hi/lo compensated
-    using T = float;
-    static constexpr int NROW = 4, NSNAP = 2, NIO = 2;  // row: h0 l0 h1 l1; planes: hi, lo
-    static constexpr bool INJECT_AHEAD = true;
-    static constexpr bool TWO_PASS = false;
-    static constexpr int NSCR = 0;
-    using Params = HeatParams;
-    static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
-        row[s] = st[j];
-        row[rs + s] = st[n + j];
-    }
-    static __device__ __forceinline__ void store_state(const T *row, int rs, int s, int64_t level, T *st,
-                                                       int64_t n, int64_t j) {
-        const int k = (int)(level & 1) * 2;
-        st[j] = row[k * rs + s];
-        st[n + j] = row[(k + 1) * rs + s];
-    }
-    static __device__ __forceinline__ void snap_out(const T *row, int rs, int s, int64_t level, T *stg, int ss,
-                                                    int e) {
-        const int k = (int)(level & 1) * 2;
-        stg[e] = row[k * rs + s];
-        stg[ss + e] = row[(k + 1) * rs + s];
-    }
-    static __device__ __forceinline__ void snap_in(T *row, int rs, int s, int64_t level, const T *stg, int ss,
-                                                   int e) {
-        const int k = (int)(level & 1) * 2;
-        row[k * rs + s] = stg[e];
-        row[(k + 1) * rs + s] = stg[ss + e];
-    }
-    static __device__ __forceinline__ void step(const Params &p, T *row, int rs, int s, int64_t level, bool gl,
-                                                bool gr) {
-        const int k = (int)(level & 1) * 2;
-        const T *h = row + k * rs;
-        const T *l = row + (k + 1) * rs;
-        HL u{h[s], l[s]};
-        HL a = gl ? u : HL{h[s - 1], l[s - 1]};
-        HL b = gr ? u : HL{h[s + 1], l[s + 1]};
-        HL o = heat_update_comp(p.rf, p.rf_lo, a, u, b);
-        const int kn = 2 - k;
-        row[kn * rs + s] = o.h;
-        row[(kn + 1) * rs + s] = o.l;
-    }
-};
-
-// ============================================================================
-// Euler
-// ============================================================================
-struct EulerParams {
-    double gamma, gm1, lam, hlam;  // gm1 = gamma - 1, hlam = lambda / 2 (rounded as FP64)
-    float gammaf, gm1f, lamf, hlamf;
-};
-
-template <class O> struct EulerK {
-    using T = typename O::T;
-    T gamma, gm1, lam, hlam;
-};
-
-template <class O>
-__device__ __forceinline__ typename O::T eu_pressure(const EulerK<O> &k, typename O::T rho, typename O::T m,
-                                                     typename O::T E) {
-    using T = typename O::T;
-    T u = O::div(m, rho);
-    return O::mul(k.gm1, O::sub(E, O::mul(O::mul(T(0.5), m), u)));
-}
-
-template <class O>
-__device__ __forceinline__ typename O::T eu_ratio(typename O::T pm, typename O::T p0, typename O::T pp) {
-    using T = typename O::T;
-    T dm = O::sub(p0, pm);
-    T dp = O::sub(pp, p0);
-    if ((dm > T(0) && dp > T(0)) || (dm < T(0) && dp < T(0))) return O::div(dm, dp);
-    return T(0);
-}
-
-template <class O>
-__device__ __forceinline__ void eu_phys_flux(const EulerK<O> &k, typename O::T rho, typename O::T m,
-                                             typename O::T E, typename O::T &f0, typename O::T &f1,
-                                             typename O::T &f2, typename O::T &speed) {
-    using T = typename O::T;
-    T u = O::div(m, rho);
-    T p = O::mul(k.gm1, O::sub(E, O::mul(O::mul(T(0.5), m), u)));
-    T c = O::sqrt_(O::div(O::mul(k.gamma, p), rho));
-    f0 = m;
-    f1 = O::add(O::mul(m, u), p);
-    f2 = O::mul(O::add(E, p), u);
-    speed = O::add(O::abs_(u), c);
-}
-
-// Numerical flux at the face between cell a (left) and cell b (right).
-template <class O>
-__device__ __forceinline__ void eu_face_flux(const EulerK<O> &k, typename O::T a0, typename O::T a1,
-                                             typename O::T a2, typename O::T tha, typename O::T b0,
-                                             typename O::T b1, typename O::T b2, typename O::T thb,
-                                             typename O::T &o0, typename O::T &o1, typename O::T &o2) {
-    using T = typename O::T;
-    T phl = tha < T(1) ? tha : T(1);
-    T phr = thb > T(1) ? O::div(T(1), thb) : (thb > T(0) ? T(1) : T(0));
-    T hl = O::mul(T(0.5), phl), hr = O::mul(T(0.5), phr);
-    T d0 = O::sub(b0, a0), d1 = O::sub(b1, a1), d2 = O::sub(b2, a2);
-    T l0 = O::add(a0, O::mul(hl, d0)), l1 = O::add(a1, O::mul(hl, d1)), l2 = O::add(a2, O::mul(hl, d2));
-    T r0 = O::sub(b0, O::mul(hr, d0)), r1 = O::sub(b1, O::mul(hr, d1)), r2 = O::sub(b2, O::mul(hr, d2));
-    T fl0, fl1, fl2, sl, fr0, fr1, fr2, sr;
-    eu_phys_flux<O>(k, l0, l1, l2, fl0, fl1, fl2, sl);
-    eu_phys_flux<O>(k, r0, r1, r2, fr0, fr1, fr2, sr);
-    T s = sl > sr ? sl : sr;
-    T hs = O::mul(T(0.5), s);
-    o0 = O::sub(O::mul(T(0.5), O::add(fl0, fr0)), O::mul(hs, O::sub(r0, l0)));
-    o1 = O::sub(O::mul(T(0.5), O::add(fl1, fr1)), O::mul(hs, O::sub(r1, l1)));
-    o2 = O::sub(O::mul(T(0.5), O::add(fl2, fr2)), O::mul(hs, O::sub(r2, l2)));
-}
-
-template <class O> __device__ __forceinline__ EulerK<O> eu_k(const EulerParams &p);
-template <> __device__ __forceinline__ EulerK<OpsD> eu_k<OpsD>(const EulerParams &p) {
-    return EulerK<OpsD>{p.gamma, p.gm1, p.lam, p.hlam};
-}
-template <> __device__ __forceinline__ EulerK<OpsF> eu_k<OpsF>(const EulerParams &p) {
-    return EulerK<OpsF>{p.gammaf, p.gm1f, p.lamf, p.hlamf};
-}
-
-// Row fields (FP64 / FP32): 0..2 Q^n, 3..5 Q*, 6 pressure ratio -- the seven values
-// per point of the lengthened state (Section 4.3). Updates are in place: a
-// sub-step reads one group of fields of its neighbours and writes another group
-// of its own, so no second buffer is needed (the alternation of Section 4.1).
-template <int PREC> struct EulerPolicy {
-    static_assert(PREC == 0 || PREC == 1, "plain Euler policy is FP64 or FP32");
-    using O = typename std::conditional<PREC == 0, OpsD, OpsF>::type;
-    using T = typename O::T;
-    static constexpr int NROW = 7, NSNAP = 7, NIO = 3;
-    static constexpr bool INJECT_AHEAD = false;
-    static constexpr bool TWO_PASS = true;
-    static constexpr int NSCR = 3;  // face flux components (or the pressure) per position
-    using Params = EulerParams;
-    static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
-        row[s] = st[j];
-        row[rs + s] = st[n + j];
-        row[2 * rs + s] = st[2 * n + j];
-    }
-    static __device__ __forceinline__ void store_state(const T *row, int rs, int s, int64_t level, T *st,
-                                                       int64_t n, int64_t j) {
-        st[j] = row[s];
-        st[n + j] = row[rs + s];
-        st[2 * n + j] = row[2 * rs + s];
-    }
-    static __device__ __forceinline__ void snap_out(const T *row, int rs, int s, int64_t level, T *stg, int ss,
-                                                    int e) {
-#pragma unroll
-        for (int f = 0; f < NSNAP; ++f) stg[f * ss + e] = row[f * rs + s];
-    }
-    static __device__ __forceinline__ void snap_in(T *row, int rs, int s, int64_t level, const T *stg, int ss,
-                                                   int e) {
-#pragma unroll
-        for (int f = 0; f < NSNAP; ++f) row[f * rs + s] = stg[f * ss + e];
-    }
-    // Two passes per sub-step (the per-cell results are those of evaluating both
-    // faces and all three pressures per cell; each is computed once here):
-    // pre():  ratio sub-steps -> p at each position in [lo-1, hi+1];
-    //         flux sub-steps  -> the face flux between positions s-1 and s, s in [lo, hi+1].
-    // step(): the cell update from the scratch values.
-    // gl: cell s is the domain's first cell; gr_prev: cell s-1 is its last (transmissive).
-    static __device__ __forceinline__ void pre(const Params &prm, const T *row, int rs, T *scr, int s,
-                                               int64_t level, int lo, int hi, int slo, int shi, bool gl,
-                                               bool gr_prev) {
-        const EulerK<O> k = eu_k<O>(prm);
-        const int kind = (int)(level & 3);
-        if (kind == 0 || kind == 2) {
-            if (s < slo || s > shi) return;
-            const T *q = row + (kind == 0 ? 0 : 3) * rs;
-            scr[s] = eu_pressure<O>(k, q[s], q[rs + s], q[2 * rs + s]);
-        } else {
-            if (s < lo) return;
-            const T *q = row + (kind == 1 ? 0 : 3) * rs;
-            const T *th = row + 6 * rs;
-            int a = s - 1, b = s;
-            T tha, thb;
-            if (gl) { a = s; tha = T(0); thb = th[s]; }
-            else if (gr_prev) { b = s - 1; tha = th[s - 1]; thb = T(0); }
-            else { tha = th[s - 1]; thb = th[s]; }
-            T f0, f1, f2;
-            eu_face_flux<O>(k, q[a], q[rs + a], q[2 * rs + a], tha, q[b], q[rs + b], q[2 * rs + b], thb, f0, f1,
-                            f2);
-            scr[s] = f0;
-            scr[rs + s] = f1;
-            scr[2 * rs + s] = f2;
-        }
-    }
-    static __device__ __forceinline__ void step(const Params &prm, T *row, int rs, const T *scr, int s,
-                                                int64_t level, bool gl, bool gr) {
-        const EulerK<O> k = eu_k<O>(prm);
-        const int kind = (int)(level & 3);
-        if (kind == 0 || kind == 2) {
-            const T pm = gl ? scr[s] : scr[s - 1], pp = gr ? scr[s] : scr[s + 1];
-            row[6 * rs + s] = eu_ratio<O>(pm, scr[s], pp);
-        } else {
-            const T c = (kind == 1) ? k.hlam : k.lam;
-            T *out = row + (kind == 1 ? 3 : 0) * rs;
-            const T q0 = row[s], q1 = row[rs + s], q2 = row[2 * rs + s];
-            out[s] = O::sub(q0, O::mul(c, O::sub(scr[s + 1], scr[s])));
-            out[rs + s] = O::sub(q1, O::mul(c, O::sub(scr[rs + s + 1], scr[rs + s])));
-            out[2 * rs + s] = O::sub(q2, O::mul(c, O::sub(scr[2 * rs + s + 1], scr[2 * rs + s])));
-        }
-    }
-};
-
-// FP32 hi/lo compensated Euler. Row fields: 0..2 Q^n high, 3..5 Q^n low, 6..8 Q*
-// (plain FP32), 9 pressure ratio. Fluxes and ratios are evaluated in FP32 from
-// the high parts; the state update Q^n - c dF is applied with TwoSum.
-struct EulerPolicyComp {
-    using O = OpsF;
-    using T = float;
-    static constexpr int NROW = 10, NSNAP = 10, NIO = 6;
-    static constexpr bool INJECT_AHEAD = false;
-    static constexpr bool TWO_PASS = true;
-    static constexpr int NSCR = 3;
-    using Params = EulerParams;
-    static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
-#pragma unroll
-        for (int f = 0; f < 6; ++f) row[f * rs + s] = st[f * n + j];
-    }
-    static __device__ __forceinline__ void store_state(const T *row, int rs, int s, int64_t level, T *st,
-                                                       int64_t n, int64_t j) {
-#pragma unroll
-        for (int f = 0; f < 6; ++f) st[f * n + j] = row[f * rs + s];
-    }
-    static __device__ __forceinline__ void snap_out(const T *row, int rs, int s, int64_t level, T *stg, int ss,
-                                                    int e) {
-#pragma unroll
-        for (int f = 0; f < NSNAP; ++f) stg[f * ss + e] = row[f * rs + s];
-    }
-    static __device__ __forceinline__ void snap_in(T *row, int rs, int s, int64_t level, const T *stg, int ss,
-                                                   int e) {
-#pragma unroll
-        for (int f = 0; f < NSNAP; ++f) row[f * rs + s] = stg[f * ss + e];
-    }
-    // Two passes per sub-step, as in EulerPolicy; fluxes and pressures from the
-    // high parts (Q^n) or the plain FP32 Q*.
-    static __device__ __forceinline__ void pre(const Params &prm, const T *row, int rs, T *scr, int s,
-                                               int64_t level, int lo, int hi, int slo, int shi, bool gl,
-                                               bool gr_prev) {
-        const EulerK<O> k = eu_k<O>(prm);
-        const int kind = (int)(level & 3);
-        if (kind == 0 || kind == 2) {
-            if (s < slo || s > shi) return;
-            const T *q = row + (kind == 0 ? 0 : 6) * rs;
-            scr[s] = eu_pressure<O>(k, q[s], q[rs + s], q[2 * rs + s]);
-        } else {
-            if (s < lo) return;
-            const T *q = row + (kind == 1 ? 0 : 6) * rs;
-            const T *th = row + 9 * rs;
-            int a = s - 1, b = s;
-            T tha, thb;
-            if (gl) { a = s; tha = T(0); thb = th[s]; }
-            else if (gr_prev) { b = s - 1; tha = th[s - 1]; thb = T(0); }
-            else { tha = th[s - 1]; thb = th[s]; }
-            T f0, f1, f2;
-            eu_face_flux<O>(k, q[a], q[rs + a], q[2 * rs + a], tha, q[b], q[rs + b], q[2 * rs + b], thb, f0, f1,
-                            f2);
-            scr[s] = f0;
-            scr[rs + s] = f1;
-            scr[2 * rs + s] = f2;
-        }
-    }
-    static __device__ __forceinline__ void step(const Params &prm, T *row, int rs, const T *scr, int s,
-                                                int64_t level, bool gl, bool gr) {
-        const EulerK<O> k = eu_k<O>(prm);
-        const int kind = (int)(level & 3);
-        if (kind == 0 || kind == 2) {
-            const T pm = gl ? scr[s] : scr[s - 1], pp = gr ? scr[s] : scr[s + 1];
-            row[9 * rs + s] = eu_ratio<O>(pm, scr[s], pp);
-        } else {
-            const T df[3] = {__fsub_rn(scr[s + 1], scr[s]), __fsub_rn(scr[rs + s + 1], scr[rs + s]),
-                             __fsub_rn(scr[2 * rs + s + 1], scr[2 * rs + s])};
-            if (kind == 1) {
-#pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    T h = row[v * rs + s], l = row[(3 + v) * rs + s];
-                    row[(6 + v) * rs + s] = __fadd_rn(h, __fsub_rn(l, __fmul_rn(k.hlam, df[v])));
-                }
-            } else {
-#pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    T h = row[v * rs + s], l = row[(3 + v) * rs + s];
-                    T delta = -__fmul_rn(k.lam, df[v]);
-                    T sm, e, nh, nl;
-                    two_sum(h, delta, sm, e);
-                    fast_two_sum(sm, __fadd_rn(l, e), nh, nl);
-                    row[v * rs + s] = nh;
-                    row[(3 + v) * rs + s] = nl;
-                }
-            }
-        }
-    }
-};
-
-}  // namespace sw
+#include "euler.cuh"
+#include "heat.cuh"
