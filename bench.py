@@ -77,8 +77,8 @@ def initial_state():
 
 # sources that define each timed kernel (a recorded traffic figure is void once they change)
 KERNEL_SOURCES = {
-    "k_heat_fold": ("common.cuh", "heat.cuh", "swept_phase.cuh", "fold_heat.cuh"),
-    "k_swept_phase": ("common.cuh", "heat.cuh", "swept_phase.cuh"),
+    "k_heat_fold": ("common.cuh", "heat.cuh", "flanks.cuh", "fold_heat.cuh"),
+    "k_swept_phase": ("common.cuh", "heat.cuh", "heat_policy.cuh", "flanks.cuh", "swept_phase.cuh"),
 }
 
 

@@ -114,15 +114,12 @@ template <int PREC> struct EulerPolicy {
         st[n + j] = row[rs + s];
         st[2 * n + j] = row[2 * rs + s];
     }
-    static __device__ __forceinline__ void snap_out(const T *row, int rs, int s, int64_t level, T *stg, int ss,
-                                                    int e) {
-#pragma unroll
-        for (int f = 0; f < NSNAP; ++f) stg[f * ss + e] = row[f * rs + s];
+    // snapshot field f of cell s (every row field is part of the snapshot)
+    static __device__ __forceinline__ T get_field(const T *row, int rs, int s, int64_t level, int f) {
+        return row[f * rs + s];
     }
-    static __device__ __forceinline__ void snap_in(T *row, int rs, int s, int64_t level, const T *stg, int ss,
-                                                   int e) {
-#pragma unroll
-        for (int f = 0; f < NSNAP; ++f) row[f * rs + s] = stg[f * ss + e];
+    static __device__ __forceinline__ void set_field(T *row, int rs, int s, int64_t level, int f, T v) {
+        row[f * rs + s] = v;
     }
     // Two passes per sub-step (the per-cell results are those of evaluating both
     // faces and all three pressures per cell; each is computed once here):
@@ -194,15 +191,12 @@ struct EulerPolicyComp {
 #pragma unroll
         for (int f = 0; f < 6; ++f) st[f * n + j] = row[f * rs + s];
     }
-    static __device__ __forceinline__ void snap_out(const T *row, int rs, int s, int64_t level, T *stg, int ss,
-                                                    int e) {
-#pragma unroll
-        for (int f = 0; f < NSNAP; ++f) stg[f * ss + e] = row[f * rs + s];
+    // snapshot field f of cell s (every row field is part of the snapshot)
+    static __device__ __forceinline__ T get_field(const T *row, int rs, int s, int64_t level, int f) {
+        return row[f * rs + s];
     }
-    static __device__ __forceinline__ void snap_in(T *row, int rs, int s, int64_t level, const T *stg, int ss,
-                                                   int e) {
-#pragma unroll
-        for (int f = 0; f < NSNAP; ++f) row[f * rs + s] = stg[f * ss + e];
+    static __device__ __forceinline__ void set_field(T *row, int rs, int s, int64_t level, int f, T v) {
+        row[f * rs + s] = v;
     }
     // Two passes per sub-step, as in EulerPolicy; fluxes and pressures from the
     // high parts (Q^n) or the plain FP32 Q*.

@@ -21,8 +21,8 @@
 // and Down triangles and any truncated phase), and the per-cell update is the
 // same function, so results are bitwise identical.
 #pragma once
+#include "flanks.cuh"
 #include "heat.cuh"
-#include "swept_phase.cuh"
 
 namespace sw {
 

@@ -46,119 +46,4 @@ struct HeatParams {
     float rf_lo;    // r - rf, rounded to float
 };
 
-// Storage policy for the swept driver. Row fields per position: two slots
-// (levels alternate between them, the "two values per point" of Section 4.1);
-// a snapshot (flank entry) is the value at one level.
-template <int PREC> struct HeatPolicy;
-
-template <> struct HeatPolicy<0> {  // FP64
-    using T = double;
-    using O = OpsD;
-    static constexpr int NROW = 2, NSNAP = 1, NIO = 1;
-    static constexpr bool INJECT_AHEAD = true;
-    static constexpr bool TWO_PASS = false;
-    static constexpr int NSCR = 0;
-    using Params = HeatParams;
-    static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
-        row[s] = st[j];
-    }
-    static __device__ __forceinline__ void store_state(const T *row, int rs, int s, int64_t level, T *st,
-                                                       int64_t n, int64_t j) {
-        st[j] = row[(level & 1) * rs + s];
-    }
-    static __device__ __forceinline__ void snap_out(const T *row, int rs, int s, int64_t level, T *stg, int ss,
-                                                    int e) {
-        stg[e] = row[(level & 1) * rs + s];
-    }
-    static __device__ __forceinline__ void snap_in(T *row, int rs, int s, int64_t level, const T *stg, int ss,
-                                                   int e) {
-        row[(level & 1) * rs + s] = stg[e];
-    }
-    static __device__ __forceinline__ void step(const Params &p, T *row, int rs, int s, int64_t level, bool gl,
-                                                bool gr) {
-        const T *cur = row + (level & 1) * rs;
-        T u = cur[s];
-        T a = gl ? u : cur[s - 1];
-        T b = gr ? u : cur[s + 1];
-        row[((level + 1) & 1) * rs + s] = heat_update<O>(p.r, a, u, b);
-    }
-};
-
-template <> struct HeatPolicy<1> {  // FP32
-    using T = float;
-    using O = OpsF;
-    static constexpr int NROW = 2, NSNAP = 1, NIO = 1;
-    static constexpr bool INJECT_AHEAD = true;
-    static constexpr bool TWO_PASS = false;
-    static constexpr int NSCR = 0;
-    using Params = HeatParams;
-    static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
-        row[s] = st[j];
-    }
-    static __device__ __forceinline__ void store_state(const T *row, int rs, int s, int64_t level, T *st,
-                                                       int64_t n, int64_t j) {
-        st[j] = row[(level & 1) * rs + s];
-    }
-    static __device__ __forceinline__ void snap_out(const T *row, int rs, int s, int64_t level, T *stg, int ss,
-                                                    int e) {
-        stg[e] = row[(level & 1) * rs + s];
-    }
-    static __device__ __forceinline__ void snap_in(T *row, int rs, int s, int64_t level, const T *stg, int ss,
-                                                   int e) {
-        row[(level & 1) * rs + s] = stg[e];
-    }
-    static __device__ __forceinline__ void step(const Params &p, T *row, int rs, int s, int64_t level, bool gl,
-                                                bool gr) {
-        const T *cur = row + (level & 1) * rs;
-        T u = cur[s];
-        T a = gl ? u : cur[s - 1];
-        T b = gr ? u : cur[s + 1];
-        row[((level + 1) & 1) * rs + s] = heat_update<O>(p.rf, a, u, b);
-    }
-};
-
-template <> struct HeatPolicy<2> {  // FP32 hi/lo compensated
-    using T = float;
-    static constexpr int NROW = 4, NSNAP = 2, NIO = 2;  // row: h0 l0 h1 l1; planes: hi, lo
-    static constexpr bool INJECT_AHEAD = true;
-    static constexpr bool TWO_PASS = false;
-    static constexpr int NSCR = 0;
-    using Params = HeatParams;
-    static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
-        row[s] = st[j];
-        row[rs + s] = st[n + j];
-    }
-    static __device__ __forceinline__ void store_state(const T *row, int rs, int s, int64_t level, T *st,
-                                                       int64_t n, int64_t j) {
-        const int k = (int)(level & 1) * 2;
-        st[j] = row[k * rs + s];
-        st[n + j] = row[(k + 1) * rs + s];
-    }
-    static __device__ __forceinline__ void snap_out(const T *row, int rs, int s, int64_t level, T *stg, int ss,
-                                                    int e) {
-        const int k = (int)(level & 1) * 2;
-        stg[e] = row[k * rs + s];
-        stg[ss + e] = row[(k + 1) * rs + s];
-    }
-    static __device__ __forceinline__ void snap_in(T *row, int rs, int s, int64_t level, const T *stg, int ss,
-                                                   int e) {
-        const int k = (int)(level & 1) * 2;
-        row[k * rs + s] = stg[e];
-        row[(k + 1) * rs + s] = stg[ss + e];
-    }
-    static __device__ __forceinline__ void step(const Params &p, T *row, int rs, int s, int64_t level, bool gl,
-                                                bool gr) {
-        const int k = (int)(level & 1) * 2;
-        const T *h = row + k * rs;
-        const T *l = row + (k + 1) * rs;
-        HL u{h[s], l[s]};
-        HL a = gl ? u : HL{h[s - 1], l[s - 1]};
-        HL b = gr ? u : HL{h[s + 1], l[s + 1]};
-        HL o = heat_update_comp(p.rf, p.rf_lo, a, u, b);
-        const int kn = 2 - k;
-        row[kn * rs + s] = o.h;
-        row[(kn + 1) * rs + s] = o.l;
-    }
-};
-
 }  // namespace sw

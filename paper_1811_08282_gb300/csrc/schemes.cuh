@@ -3,3 +3,4 @@
 #pragma once
 #include "euler.cuh"
 #include "heat.cuh"
+#include "heat_policy.cuh"

@@ -20,6 +20,7 @@
 // per-step launches.
 #pragma once
 #include "common.cuh"
+#include "flanks.cuh"
 
 namespace sw {
 
@@ -41,26 +42,20 @@ template <class T> struct PhaseArgs {
     T *state;            // state planes (layout of the policy)
 };
 
-// Flank buffer element ((f * S + b) * 2 + side) * W + (2*j + k):
-// field f, structure b, side 0 = left / 1 = right, level offset j, cell k of the pair.
-template <class T>
-__device__ __forceinline__ int64_t flank_off(int64_t S, int W, int f, int64_t b, int side) {
-    return ((f * S + b) * 2 + side) * (int64_t)W;
-}
-
 // Flank loads: plain within a launch sequence (the L1 is not reused across
 // launches); L2-only (ld.global.cg) inside a persistent kernel, where another CTA
 // may have rewritten a flank that this SM's L1 still holds from an earlier item.
+// Values are read one flank pair per level, prefetched a level ahead.
 template <bool CG, class T> __device__ __forceinline__ T flank_ld(const T *p) {
     if constexpr (CG) return __ldcg(p);
     else return *p;
 }
 
 // Shared memory of one structure, in elements of P::T: the row (NROW fields of
-// W+2 positions), the flank stage (NSNAP fields of 2W) and, for two-pass
-// policies, per-position scratch (NSCR fields of W+2).
+// W+2 positions) and, for two-pass policies, per-position scratch (NSCR fields
+// of W+2). Flanks go between global memory and the row directly.
 template <class P> __host__ __device__ constexpr size_t swept_smem_elems(int W) {
-    return size_t(P::NROW) * (W + 2) + size_t(P::NSNAP) * 2 * W + size_t(P::NSCR) * (W + 2);
+    return size_t(P::NROW) * (W + 2) + size_t(P::NSCR) * (W + 2);
 }
 
 // One sub-step over row positions [lo, hi]: two-pass policies first compute
@@ -96,11 +91,10 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
     T *row = smem;
     const int W = a.W, H = a.H;
     const int rs = W + 2;                 // row stride (positions 0..W+1)
-    T *stage = row + P::NROW * rs;        // [NSNAP][2 sides][W]
-    const int ss = 2 * W;                 // stage field stride
-    T *scr = stage + P::NSNAP * ss;       // [NSCR][W+2] (two-pass policies)
+    T *scr = row + P::NROW * rs;          // [NSCR][W+2] (two-pass policies)
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t n = a.n;
+    const int64_t S = a.nstruct_max;
     const int64_t c = (a.p & 1) ? b * W : b * W + H;
     const int64_t base = c - H - 1;       // cell of row position 0
 
@@ -113,18 +107,22 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
     auto cell = [&](int s) -> int64_t { return a.periodic ? wrap_index(base + s, n) : base + s; };
     auto ghost_l = [&](int s) -> bool { return !a.periodic && base + s == 0; };
     auto ghost_r = [&](int s) -> bool { return !a.periodic && base + s == n - 1; };
+    // this structure's flank entry e of `side` (0 left, 1 right) at level `lev`: every field
+    auto publish = [&](int s, int64_t lev, int side, int e) {
+        if (!a.flank_out || a.upper <= 0) return;
+#pragma unroll
+        for (int f = 0; f < P::NSNAP; ++f)
+            a.flank_out[flank_off<T>(S, W, f, b, side) + e] = P::get_field(row, rs, s, lev, f);
+    };
 
     if (a.p == 0) {
         // Up Triangle: the initial row [c-H, c+H) at level 0 (always inside the domain)
         for (int s = 1 + tid; s <= W; s += nt) {
             P::load_state(row, rs, s, a.state, n, base + s);
-        }
-        __syncthreads();
-        // flank entries of level 0 (j = 0): cells s = 1, 2 (left) and W-1, W (right)
-        if (tid < 4) {
-            const int side = tid >> 1, k = tid & 1;
-            const int s = side == 0 ? 1 + k : W - 1 + k;
-            P::snap_out(row, rs, s, 0, stage, ss, side * W + k);
+            if (s == 1) publish(s, 0, 0, 0);      // flank entries of level 0 (j = 0)
+            if (s == 2) publish(s, 0, 0, 1);
+            if (s == W - 1) publish(s, 0, 1, 0);
+            if (s == W) publish(s, 0, 1, 1);
         }
         __syncthreads();
     } else {
@@ -140,27 +138,36 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
         } else {
             if (a.p & 1) { has_l = b > 0; has_r = b < a.tiles; }
         }
-        // stage: side 0 <- left neighbour's right flank, side 1 <- right neighbour's left flank
-        const int64_t S = a.nstruct_max;
-        for (int f = 0; f < P::NSNAP; ++f) {
-            if (has_l) {
-                const T *src = a.flank_in + flank_off<T>(S, W, f, lb, 1);
-                for (int e = tid; e < W; e += nt) stage[f * ss + e] = flank_ld<CG>(src + e);
-            }
-            if (has_r) {
-                const T *src = a.flank_in + flank_off<T>(S, W, f, rb, 0);
-                for (int e = tid; e < W; e += nt) stage[f * ss + W + e] = flank_ld<CG>(src + e);
+        // Communication: the flank pair of step i (level F-H+i-1) goes straight from the
+        // neighbours' flanks into the row -- slot t = (side, k, field), at most two per
+        // thread -- each value prefetched into a register one step ahead.
+        constexpr int NSLOT = 4 * P::NSNAP;
+        T pv[2] = {T(0), T(0)};
+        const T *src[2] = {nullptr, nullptr};
+        int pos_k[2] = {0, 0}, side_[2] = {0, 0}, fld[2] = {0, 0};
+        bool use[2] = {false, false};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int t = tid + q * nt;
+            if (t < NSLOT) {
+                side_[q] = t / (2 * P::NSNAP);
+                const int rem = t % (2 * P::NSNAP);
+                pos_k[q] = rem / P::NSNAP;
+                fld[q] = rem % P::NSNAP;
+                use[q] = side_[q] == 0 ? has_l : has_r;
+                if (use[q]) {
+                    src[q] = a.flank_in + flank_off<T>(S, W, fld[q], side_[q] == 0 ? lb : rb, side_[q] == 0 ? 1 : 0);
+                    if (a.lower > 0) pv[q] = flank_ld<CG>(src[q] + pos_k[q]);
+                }
             }
         }
-        __syncthreads();
-        // inject the flank pair for step i (level F-H+i-1) into the row
         auto inject = [&](int i) {
-            if (tid < 4) {
-                const int side = tid >> 1, k = tid & 1;
-                const int s = side == 0 ? H - i + k : H + i + k;
-                const bool ok = side == 0 ? has_l : has_r;
-                if (ok && s >= slo && s <= shi)
-                    P::snap_in(row, rs, s, a.F - H + i - 1, stage, ss, side * W + 2 * (i - 1) + k);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (!use[q]) continue;
+                const int s = side_[q] == 0 ? H - i + pos_k[q] : H + i + pos_k[q];
+                if (s >= slo && s <= shi) P::set_field(row, rs, s, a.F - H + i - 1, fld[q], pv[q]);
+                if (i < a.lower) pv[q] = flank_ld<CG>(src[q] + 2 * i + pos_k[q]);
             }
         };
         if (P::INJECT_AHEAD && a.lower > 0) {
@@ -178,11 +185,11 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
             if (hi > shi) hi = shi;
             const bool last = (i == a.lower);
             swept_level<P>(prm, row, rs, scr, lev, lo, hi, slo, shi, ghost_l, ghost_r, [&](int s) {
-                if (i == H && a.upper > 0) {  // full level F reached: flank entries j = 0
-                    if (s == 1) P::snap_out(row, rs, s, lev + 1, stage, ss, 0);
-                    if (s == 2) P::snap_out(row, rs, s, lev + 1, stage, ss, 1);
-                    if (s == W - 1) P::snap_out(row, rs, s, lev + 1, stage, ss, W);
-                    if (s == W) P::snap_out(row, rs, s, lev + 1, stage, ss, W + 1);
+                if (i == H) {  // full level F reached: flank entries j = 0
+                    if (s == 1) publish(s, lev + 1, 0, 0);
+                    if (s == 2) publish(s, lev + 1, 0, 1);
+                    if (s == W - 1) publish(s, lev + 1, 1, 0);
+                    if (s == W) publish(s, lev + 1, 1, 1);
                 }
                 if (last && a.write_lower) P::store_state(row, rs, s, lev + 1, a.state, n, cell(s));
             });
@@ -191,7 +198,7 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
         }
     }
 
-    // upper half: levels F+1 .. F+upper on the narrowing window
+    // upper half: levels F+1 .. F+upper on the narrowing window; flank entries j = i
     for (int i = 1; i <= a.upper; ++i) {
         const int64_t lev = a.F + i - 1;
         int lo = 1 + i, hi = W - i;
@@ -199,26 +206,13 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
         if (hi > shi) hi = shi;
         const bool last = (i == a.upper);
         swept_level<P>(prm, row, rs, scr, lev, lo, hi, slo, shi, ghost_l, ghost_r, [&](int s) {
-            if (s == 1 + i) P::snap_out(row, rs, s, lev + 1, stage, ss, 2 * i);
-            if (s == 2 + i) P::snap_out(row, rs, s, lev + 1, stage, ss, 2 * i + 1);
-            if (s == W - 1 - i) P::snap_out(row, rs, s, lev + 1, stage, ss, W + 2 * i);
-            if (s == W - i) P::snap_out(row, rs, s, lev + 1, stage, ss, W + 2 * i + 1);
+            if (s == 1 + i) publish(s, lev + 1, 0, 2 * i);
+            if (s == 2 + i) publish(s, lev + 1, 0, 2 * i + 1);
+            if (s == W - 1 - i) publish(s, lev + 1, 1, 2 * i);
+            if (s == W - i) publish(s, lev + 1, 1, 2 * i + 1);
             if (last && a.write_upper) P::store_state(row, rs, s, lev + 1, a.state, n, cell(s));
         });
         __syncthreads();
-    }
-
-    // publish this structure's flanks for the next phase
-    if (a.upper > 0 && a.flank_out) {
-        const int64_t S = a.nstruct_max;
-        for (int f = 0; f < P::NSNAP; ++f) {
-            T *dl = a.flank_out + flank_off<T>(S, W, f, b, 0);
-            T *dr = a.flank_out + flank_off<T>(S, W, f, b, 1);
-            for (int e = tid; e < W; e += nt) {
-                dl[e] = stage[f * ss + e];
-                dr[e] = stage[f * ss + W + e];
-            }
-        }
     }
 }
 
