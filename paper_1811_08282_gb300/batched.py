@@ -4,14 +4,14 @@
     bt = batched.build(batched.default_items(4096, seed=7), nsteps=10_000)
     bt.batch.sw_batch_run(); bt.batch.sw_batch_status()
 
-Tile widths come from the library's autotuner (sw_autotune: short timed runs per
-width, Section 6's advice) applied once per (scheme, power-of-two size class) and
-then fitted to each problem's length (largest tuned-or-smaller width that divides
-it). Heat problems are periodic, Euler problems transmissive Riemann problems.
+Tile widths are tuned as one cap per scheme by timing the batch kernel itself on
+short runs of a GPU-filling sample of the items (Section 6's advice: tune on a few
+short runs), then fitted to each problem's length (largest width <= the cap that
+divides it and leaves at least two tiles). Heat problems are periodic, Euler
+problems transmissive Riemann problems.
 """
 from __future__ import annotations
 
-import math
 from dataclasses import dataclass, field
 
 from . import inputs as I
@@ -24,7 +24,7 @@ class BuiltBatch:
     problems: list
     states: list
     items: list
-    widths: dict = field(default_factory=dict)  # (scheme, size class) -> tuned width
+    widths: dict = field(default_factory=dict)  # scheme -> tuned width cap
 
     @property
     def cells(self) -> int:
@@ -44,16 +44,48 @@ def _problem(item, precision, W, flags=0):
                      n=item.n, dt_dx=I.riemann_lambda(), gamma=I.GAMMA, tile_width=W, flags=flags)
 
 
-def tune_widths(items, precision=S.SW_FP32_COMP, probe_steps: int = 256):
-    """Tuned width per (scheme, size class 2^k), measured on a length-2^k problem."""
+def tune_widths(items, precision=S.SW_FP32_COMP, candidates=(256, 512, 1024), sample_cells: int = 1 << 24):
+    """One tile-width cap per scheme, chosen by timing the batch kernel itself on
+    short runs (Section 6: tune W on a few short runs).
+
+    For each scheme, a prefix of that scheme's items totalling about `sample_cells`
+    cells (all of them when there are fewer) runs as its own batch once per
+    candidate cap, each problem at the largest width <= the cap that fits it. The
+    items are already in random order, so the prefix keeps the length mix; it is
+    large enough to give every SM several work items per phase, as the whole batch
+    does, so queue and occupancy effects are part of what is timed (a few small
+    probe problems would leave most SMs idle and favour narrow tiles). Each timed
+    run covers two phases of the widest candidate, after one untimed run of the
+    same length. Returns {scheme: width cap}."""
+    import torch
     widths = {}
-    for it in items:
-        k = int(round(math.log2(it.n)))
-        key = (it.scheme, k)
-        if key in widths:
-            continue
-        probe = _problem(I.BatchItem(it.scheme, 1 << k, 0.3, None), precision, 0, flags=S.SW_FLAG_GENERIC)
-        widths[key] = S.sw_autotune(probe, probe_steps)
+    for scheme in sorted({it.scheme for it in items}):
+        sample, cells = [], 0
+        for it in items:
+            if it.scheme == scheme and cells < sample_cells:
+                sample.append(it)
+                cells += it.n
+        levels = max(candidates)
+        steps = levels if scheme == "heat" else levels // 4
+        best = None
+        for cap in candidates:
+            probs = [_problem(it, precision, fit_width(it.n, cap)) for it in sample]
+            states = [S.to_state(p, torch.as_tensor(it.planes.reshape(-1), device="cuda"))
+                      for p, it in zip(probs, sample)]
+            with S.Batch(probs, states, steps) as b:
+                b.sw_batch_run()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                b.sw_batch_run()
+                e1.record()
+                e1.synchronize()
+                t = e0.elapsed_time(e1)
+                if b.sw_batch_status() != S.SW_OK:
+                    continue
+            if best is None or t < best[0]:
+                best = (t, cap)
+        widths[scheme] = best[1] if best else 256
     return widths
 
 
@@ -69,8 +101,7 @@ def build(items, nsteps: int, precision=S.SW_FP32_COMP, widths=None) -> BuiltBat
     widths = widths if widths is not None else tune_widths(items, precision)
     problems, states = [], []
     for it in items:
-        k = int(round(math.log2(it.n)))
-        W = fit_width(it.n, widths[(it.scheme, k)])
+        W = fit_width(it.n, widths[it.scheme])
         p = _problem(it, precision, W)
         problems.append(p)
         states.append(S.to_state(p, torch.as_tensor(it.planes.reshape(-1), device="cuda")))

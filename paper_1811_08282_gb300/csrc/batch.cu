@@ -93,7 +93,7 @@ __device__ __forceinline__ int64_t upper_index(const int64_t *v, int64_t lo, int
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kBatchThreads) k_batch(BatchTables t) {
+__global__ void __launch_bounds__(kBatchThreads, PREC == 0 ? 4 : 8) k_batch(BatchTables t) {
     using HP = HeatPolicy<PREC>;
     using EP = typename EulerPolicyOf<PREC>::type;
     using T = typename HP::T;

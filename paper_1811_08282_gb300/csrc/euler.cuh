@@ -102,6 +102,8 @@ template <int PREC> struct EulerPolicy {
     static constexpr bool INJECT_AHEAD = false;
     static constexpr bool TWO_PASS = true;
     static constexpr int NSCR = 3;  // face flux components (or the pressure) per position
+    // launch bound: FP32 keeps 64 registers (4 CTAs of 256 threads per SM), FP64 up to 128
+    static constexpr int MIN_BLOCKS = PREC == 0 ? 1 : 2;
     using Params = EulerParams;
     static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
         row[s] = st[j];
@@ -181,6 +183,7 @@ struct EulerPolicyComp {
     static constexpr bool INJECT_AHEAD = false;
     static constexpr bool TWO_PASS = true;
     static constexpr int NSCR = 3;
+    static constexpr int MIN_BLOCKS = 2;
     using Params = EulerParams;
     static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
 #pragma unroll

@@ -17,6 +17,7 @@ template <> struct HeatPolicy<0> {  // FP64
     static constexpr bool INJECT_AHEAD = true;
     static constexpr bool TWO_PASS = false;
     static constexpr int NSCR = 0;
+    static constexpr int MIN_BLOCKS = 4;  // launch bound: resident 512-thread blocks per SM
     using Params = HeatParams;
     static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
         row[s] = st[j];
@@ -49,6 +50,7 @@ template <> struct HeatPolicy<1> {  // FP32
     static constexpr bool INJECT_AHEAD = true;
     static constexpr bool TWO_PASS = false;
     static constexpr int NSCR = 0;
+    static constexpr int MIN_BLOCKS = 4;  // launch bound: resident 512-thread blocks per SM
     using Params = HeatParams;
     static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
         row[s] = st[j];
@@ -80,6 +82,7 @@ template <> struct HeatPolicy<2> {  // FP32 hi/lo compensated
     static constexpr bool INJECT_AHEAD = true;
     static constexpr bool TWO_PASS = false;
     static constexpr int NSCR = 0;
+    static constexpr int MIN_BLOCKS = 3;  // launch bound: resident 512-thread blocks per SM
     using Params = HeatParams;
     static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
         row[s] = st[j];

@@ -45,17 +45,21 @@ template <class T> struct PhaseArgs {
 // Flank loads: plain within a launch sequence (the L1 is not reused across
 // launches); L2-only (ld.global.cg) inside a persistent kernel, where another CTA
 // may have rewritten a flank that this SM's L1 still holds from an earlier item.
-// Values are read one flank pair per level, prefetched a level ahead.
+// Input entries are staged in chunks of levels (kFlankChunk).
 template <bool CG, class T> __device__ __forceinline__ T flank_ld(const T *p) {
     if constexpr (CG) return __ldcg(p);
     else return *p;
 }
 
+// Levels of neighbour flank entries staged per cooperative load.
+constexpr int kFlankChunk = 32;
+
 // Shared memory of one structure, in elements of P::T: the row (NROW fields of
-// W+2 positions) and, for two-pass policies, per-position scratch (NSCR fields
-// of W+2). Flanks go between global memory and the row directly.
+// W+2 positions), for two-pass policies per-position scratch (NSCR fields of
+// W+2), and a chunk of staged input flank entries. Output flank entries go from
+// the row to global memory directly.
 template <class P> __host__ __device__ constexpr size_t swept_smem_elems(int W) {
-    return size_t(P::NROW) * (W + 2) + size_t(P::NSCR) * (W + 2);
+    return size_t(P::NROW) * (W + 2) + size_t(P::NSCR) * (W + 2) + size_t(P::NSNAP) * 4 * (kFlankChunk + 1);
 }
 
 // One sub-step over row positions [lo, hi]: two-pass policies first compute
@@ -92,6 +96,7 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
     const int W = a.W, H = a.H;
     const int rs = W + 2;                 // row stride (positions 0..W+1)
     T *scr = row + P::NROW * rs;          // [NSCR][W+2] (two-pass policies)
+    T *chunk = scr + P::NSCR * rs;        // [NSNAP][2 sides][2 (kFlankChunk + 1)] staged flank entries
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t n = a.n;
     const int64_t S = a.nstruct_max;
@@ -138,44 +143,45 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
         } else {
             if (a.p & 1) { has_l = b > 0; has_r = b < a.tiles; }
         }
-        // Communication: the flank pair of step i (level F-H+i-1) goes straight from the
-        // neighbours' flanks into the row -- slot t = (side, k, field), at most two per
-        // thread -- each value prefetched into a register one step ahead.
-        constexpr int NSLOT = 4 * P::NSNAP;
-        T pv[2] = {T(0), T(0)};
-        const T *src[2] = {nullptr, nullptr};
-        int pos_k[2] = {0, 0}, side_[2] = {0, 0}, fld[2] = {0, 0};
-        bool use[2] = {false, false};
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int t = tid + q * nt;
-            if (t < NSLOT) {
-                side_[q] = t / (2 * P::NSNAP);
-                const int rem = t % (2 * P::NSNAP);
-                pos_k[q] = rem / P::NSNAP;
-                fld[q] = rem % P::NSNAP;
-                use[q] = side_[q] == 0 ? has_l : has_r;
-                if (use[q]) {
-                    src[q] = a.flank_in + flank_off<T>(S, W, fld[q], side_[q] == 0 ? lb : rb, side_[q] == 0 ? 1 : 0);
-                    if (a.lower > 0) pv[q] = flank_ld<CG>(src[q] + pos_k[q]);
-                }
-            }
-        }
-        auto inject = [&](int i) {
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (!use[q]) continue;
-                const int s = side_[q] == 0 ? H - i + pos_k[q] : H + i + pos_k[q];
-                if (s >= slo && s <= shi) P::set_field(row, rs, s, a.F - H + i - 1, fld[q], pv[q]);
-                if (i < a.lower) pv[q] = flank_ld<CG>(src[q] + 2 * i + pos_k[q]);
+        // Communication: the neighbours' flank entries are staged in chunks of CH levels
+        // (all fields, both sides, one overlapping entry pair so that an injection one
+        // level ahead stays inside the chunk), loaded cooperatively from global memory;
+        // step i injects the flank pair of level F-H+i-1 from the chunk into the row.
+        const int cs = 2 * (kFlankChunk + 1);  // entries per (field, side) in the chunk
+        int i0 = 1;                            // first step the chunk serves
+        auto load_chunk = [&](int first) {
+            i0 = first;
+            for (int t = tid; t < P::NSNAP * 2 * cs; t += nt) {
+                const int f = t / (2 * cs), rem = t % (2 * cs), side = rem / cs, e = rem % cs;
+                const int64_t idx = 2 * (int64_t)(first - 1) + e;
+                if (idx < W && (side == 0 ? has_l : has_r))
+                    chunk[t] = flank_ld<CG>(a.flank_in +
+                                            flank_off<T>(S, W, f, side == 0 ? lb : rb, side == 0 ? 1 : 0) + idx);
             }
         };
+        auto inject = [&](int i) {
+            for (int t = tid; t < 4 * P::NSNAP; t += nt) {
+                const int side = t / (2 * P::NSNAP), rem = t % (2 * P::NSNAP);
+                const int k = rem / P::NSNAP, f = rem % P::NSNAP;
+                const int s = side == 0 ? H - i + k : H + i + k;
+                if ((side == 0 ? has_l : has_r) && s >= slo && s <= shi)
+                    P::set_field(row, rs, s, a.F - H + i - 1, f, chunk[(f * 2 + side) * cs + 2 * (i - i0) + k]);
+            }
+        };
+        if (a.lower > 0) {
+            load_chunk(1);
+            __syncthreads();
+        }
         if (P::INJECT_AHEAD && a.lower > 0) {
             inject(1);
             __syncthreads();
         }
         for (int i = 1; i <= a.lower; ++i) {
             const int64_t lev = a.F - H + i - 1;  // level read; level lev+1 written
+            if (i > 1 && (i - 1) % kFlankChunk == 0) {  // the previous level ended with a barrier
+                load_chunk(i);
+                __syncthreads();
+            }
             if (!P::INJECT_AHEAD) {
                 inject(i);
                 __syncthreads();
@@ -217,7 +223,8 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
 }
 
 template <class P>
-__global__ void __launch_bounds__(512) k_swept_phase(PhaseArgs<typename P::T> a, typename P::Params prm) {
+__global__ void __launch_bounds__(512, P::MIN_BLOCKS) k_swept_phase(PhaseArgs<typename P::T> a,
+                                                                    typename P::Params prm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     swept_structure<P, false>(a, prm, (int64_t)blockIdx.x, reinterpret_cast<typename P::T *>(smem_raw));
 }
