@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--configs", action="store_true",
+                    help="instead of the headline, time the other paper-shaped workloads (one JSON line each)")
     return ap.parse_args()
 
 
@@ -375,6 +377,27 @@ def run_ours(args):
                                "status": bt.batch.sw_batch_status(), "precision": "fp32_comp"}
     bt.batch.close()
 
+    # FP64 conservation sums (fixed-order tree) over the N = 2^24 state: the whole call,
+    # two reduction launches and the 8-byte read-back, timed on the stream (L2 flushed)
+    pc = problem(S.SW_FP64, S.SW_SWEPT, best_w)
+    stc = S.to_state(pc, u0_dev)
+    with S.Handle(pc) as hc:
+        hc.sw_conservation(stc, stream)
+        tcs = []
+        for _ in range(5):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            hc.sw_conservation(stc, stream)
+            b.record(stream)
+            b.synchronize()
+            tcs.append(a.elapsed_time(b) / 1e3)
+    tc = min(tcs)
+    compare["conservation_fp64_n2^24"] = {"us": tc * 1e6, "hbm_gbs": N * 8 / tc / 1e9,
+                                          "note": "sw_conservation call incl. read-back of the sum"}
+    del stc
+
     perstep_bytes = 16  # FP64 per-step: read + write one value per update
     compare["fp64_perstep"]["hbm_gbs"] = compare["fp64_perstep"]["value"] * perstep_bytes
     compare["speedup_swept_over_perstep_fp64"] = compare["fp64_swept"]["value"] / compare["fp64_perstep"]["value"]
@@ -473,10 +496,141 @@ def run_reference(args):
     }))
 
 
+def run_configs(args):
+    """Rates of the paper-shaped workloads besides the headline, each swept and per-step
+    at FP64, FP32 and FP32 hi/lo, with the FP32 forms' error against the FP64 result
+    (the FP64 path is bitwise equal to the oracle for Euler and within 1e-12 of the
+    oracle's closed form for heat; the full-size parity tests check that on these
+    workloads, Euler on the window the waves reach or on a shorter run). One untimed
+    short run per handle first; single timed run per form (long runs)."""
+    import numpy as np
+    import torch
+    from paper_1811_08282_gb300 import build, batched
+    build.build()
+    from paper_1811_08282_gb300 import swept as S, inputs as I
+    rank, local_rank, world = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    precs = {"fp64": S.SW_FP64, "fp32": S.SW_FP32, "fp32_comp": S.SW_FP32_COMP}
+
+    def timed(p, x0, steps, warm=8):
+        st = S.to_state(p, torch.as_tensor(x0.reshape(-1), device="cuda"))
+        fresh = st.clone()
+        with S.Handle(p) as h:
+            h.sw_run(st, warm)
+            st.copy_(fresh)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            h.sw_run(st, steps)
+            b.record()
+            b.synchronize()
+            rc = h.sw_sync_status()
+            launches = h.sw_last_launch_count()
+        if rc < 0:
+            raise S.SweptError(rc, "configs")
+        return a.elapsed_time(b) / 1e3, S.to_fp64(p, st).cpu().numpy().reshape(p.nv, p.n), launches
+
+    def errors(got, ref):
+        out = {}
+        for v in range(ref.shape[0]):
+            d = np.abs(got[v] - ref[v])
+            out[f"v{v}"] = {"max_rel": float(d.max() / np.abs(ref[v]).max()),
+                            "l2_rel": float(np.linalg.norm(d) / np.linalg.norm(ref[v]))}
+        return out
+
+    def best_width(make, x0, steps, widths=(64, 128, 256, 512, 1024)):
+        n = x0.shape[-1]
+        rates = {}
+        for W in widths:
+            if n % W or n < 2 * W:
+                continue
+            t, _, _ = timed(make(W), x0, steps)
+            rates[W] = t
+        return min(rates, key=rates.get)
+
+    def compare(name, make, x0, steps, tune_steps, extra):
+        res = {"config": name, "n": x0.shape[-1], "steps": steps, **extra, "forms": {}}
+        ref = None
+        for pn, pv in precs.items():
+            W = best_width(lambda W: make(pv, S.SW_SWEPT, W), x0, tune_steps)
+            ts, xs, ls = timed(make(pv, S.SW_SWEPT, W), x0, steps)
+            tp, xp, lp = timed(make(pv, S.SW_PERSTEP, 0), x0, steps)
+            form = {"W": W, "swept": x0.shape[-1] * steps / ts / 1e9, "perstep": x0.shape[-1] * steps / tp / 1e9,
+                    "speedup": tp / ts, "launches_swept": ls, "launches_perstep": lp,
+                    "swept_equals_perstep": bool(np.array_equal(xs, xp))}
+            if pn == "fp64":
+                ref = xs
+            else:
+                form["err_vs_fp64"] = errors(xs, ref)
+            res["forms"][pn] = form
+            print(f"# {name} {pn} done", file=sys.stderr, flush=True)
+        res["unit"] = "Gcell-steps/s"
+        print(json.dumps(res), flush=True)
+
+    # small grid: heat N = 16384, r = 0.25, 8 modes, seeds 0-4, 1000 steps, W = 64 vs per-step
+    n, steps = 16384, 1000
+    rows = []
+    for seed in range(5):
+        x0 = I.heat_initial(I.heat_modes(n, 8, seed=seed))[None]
+        row = {}
+        for pn in ("fp64", "fp32"):
+            mk = lambda m, W: S.Problem(scheme=S.SW_HEAT, precision=precs[pn], boundary=S.SW_PERIODIC, method=m,
+                                        n=n, r=0.25, tile_width=W)
+            ts, xs, _ = timed(mk(S.SW_SWEPT, 64), x0, steps)
+            tp, xp, _ = timed(mk(S.SW_PERSTEP, 0), x0, steps)
+            row[pn] = {"swept_ms": ts * 1e3, "perstep_ms": tp * 1e3, "speedup": tp / ts,
+                       "swept_equals_perstep": bool(np.array_equal(xs, xp))}
+        rows.append(row)
+    print(json.dumps({"config": "heat N=16384 r=0.25 8 modes seeds 0-4, 1000 steps, W=64", "seeds": rows,
+                      "mean_speedup_fp64": statistics.mean(r["fp64"]["speedup"] for r in rows),
+                      "mean_speedup_fp32": statistics.mean(r["fp32"]["speedup"] for r in rows)}), flush=True)
+
+    # Euler Sod, N = 2^20, 20,000 steps, transmissive
+    def euler(lam):
+        return lambda pv, m, W: S.Problem(scheme=S.SW_EULER, precision=pv, boundary=S.SW_TRANSMISSIVE, method=m,
+                                          n=1 << 20 if lam == "sod" else 1 << 22,
+                                          dt_dx=I.sod_lambda() if lam == "sod" else I.riemann_lambda(),
+                                          gamma=I.GAMMA, tile_width=W)
+    compare("Euler Sod N=2^20, 20000 steps, transmissive", euler("sod"), I.sod(1 << 20), 20_000, 512,
+            {"dt_dx": I.sod_lambda()})
+
+    # precision config: heat N = 2^22, r = 0.4, 100,000 steps; Euler N = 2^22, 64 random Riemann segments
+    n = 1 << 22
+    heat = lambda pv, m, W: S.Problem(scheme=S.SW_HEAT, precision=pv, boundary=S.SW_PERIODIC, method=m, n=n,
+                                      r=0.4, tile_width=W)
+    compare("heat N=2^22 r=0.4, 100000 steps, 32 modes", heat, I.heat_initial(I.heat_modes(n, 32, seed=1))[None],
+            100_000, 4096, {"r": 0.4})
+    compare("Euler N=2^22, 64 random Riemann segments, 20000 steps, transmissive", euler("riemann"),
+            I.riemann_initial(I.riemann_segments(n, 64, 1)), 20_000, 512, {"dt_dx": I.riemann_lambda()})
+
+    # batched: 4096 problems, FP32 hi/lo, tuned widths, 10,000 steps in one persistent launch
+    items = batched.default_items(4096, seed=7)
+    t0 = time.perf_counter()
+    widths = batched.tune_widths(items)
+    tune_s = time.perf_counter() - t0
+    bt = batched.build(items, 10_000, widths=widths)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    bt.batch.sw_batch_run()
+    b.record()
+    b.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    print(json.dumps({"config": "batched 4096 problems, lengths log-uniform 2^10..2^18, half heat / half Euler, "
+                      "FP32 hi/lo, 10000 steps", "cells": bt.cells, "widths": widths, "tune_s": tune_s,
+                      "seconds": t, "value": bt.cells * 10_000 / t / 1e9, "unit": "Gcell-steps/s",
+                      "items": bt.batch.sw_batch_items(), "status": bt.batch.sw_batch_status()}), flush=True)
+    bt.batch.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.configs:
+        run_configs(args)
     else:
         run_ours(args)
 

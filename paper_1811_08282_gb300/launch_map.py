@@ -1,0 +1,143 @@
+"""Launch-condition map and power-law fit of the swept rule on one GPU.
+
+Section 5 maps the time per time step of Swept and Classic over the launch
+conditions (threads per block, i.e. tile width W) and grid size N, then takes
+the best W per N and fits the Swept time per step to a power law y = A x^b
+(Table 1, least squares, with R^2). This module runs that experiment on this
+library: every (N, W) for the swept method, and the per-step ("Classic") kernel
+once per N (it has no tile width), each timed with CUDA events after one
+untimed run. There is no GPU work factor here: the whole domain is on the GPU.
+
+    python -m paper_1811_08282_gb300.launch_map --scheme heat --precision fp64
+    python -m paper_1811_08282_gb300.launch_map --scheme euler --precision fp64 --exps 14 20
+
+Output: one JSON line per measurement ({"kind": "point", ...}), one per N with
+the best W and the swept speedup over per-step ({"kind": "best", ...}), and one
+with the fit ({"kind": "fit", "A_us": A, "b": b, "r2": R^2}), where the fit is
+ordinary least squares of log y on log x and R^2 is taken in that log space.
+Heat uses 32 sine modes (r = 0.3, periodic); Euler the Sod problem (transmissive).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+
+from . import inputs as I
+from . import swept as S
+
+PREC = {"fp64": S.SW_FP64, "fp32": S.SW_FP32, "fp32_comp": S.SW_FP32_COMP}
+
+
+def power_fit(xs, ys):
+    """Least-squares fit of log y = log A + b log x; returns (A, b, R^2 in log space)."""
+    lx = [math.log(x) for x in xs]
+    ly = [math.log(y) for y in ys]
+    n = len(lx)
+    mx, my = sum(lx) / n, sum(ly) / n
+    sxx = sum((a - mx) ** 2 for a in lx)
+    sxy = sum((a - mx) * (b - my) for a, b in zip(lx, ly))
+    b = sxy / sxx
+    a = my - b * mx
+    ss_res = sum((y - (a + b * x)) ** 2 for x, y in zip(lx, ly))
+    ss_tot = sum((y - my) ** 2 for y in ly)
+    return math.exp(a), b, (1.0 - ss_res / ss_tot) if ss_tot > 0 else 1.0
+
+
+def steps_for(scheme: str, n: int, target: float, wmax: int, cap: int) -> int:
+    """Time steps for one measurement: about `target` cell-steps, at least four
+    phases of the widest tile (W/2 levels per phase; Euler has 4 levels per step),
+    at most `cap`."""
+    lo = 2 * wmax if scheme == "heat" else wmax // 2
+    return int(min(max(lo, target // n), max(lo, cap)))
+
+
+def _problem(scheme, precision, n, method, W):
+    if scheme == "heat":
+        return S.Problem(scheme=S.SW_HEAT, precision=precision, boundary=S.SW_PERIODIC, method=method,
+                         n=n, r=0.3, tile_width=W)
+    return S.Problem(scheme=S.SW_EULER, precision=precision, boundary=S.SW_TRANSMISSIVE, method=method,
+                     n=n, dt_dx=I.sod_lambda(), gamma=I.GAMMA, tile_width=W)
+
+
+def _initial(scheme, n):
+    if scheme == "heat":
+        return I.heat_initial(I.heat_modes(n, 32, seed=1))[None]
+    return I.sod(n)
+
+
+def measure(scheme: str, precision: int, n: int, method: int, W: int, steps: int, reps: int) -> float:
+    """Seconds per run of `steps` time steps (minimum over `reps` timed runs after one
+    untimed run), state resident on the device, reset from a device copy each run."""
+    import torch
+    p = _problem(scheme, precision, n, method, W)
+    x0 = torch.as_tensor(_initial(scheme, n).reshape(-1), device="cuda")
+    fresh = S.to_state(p, x0)
+    st = fresh.clone()
+    ts = []
+    with S.Handle(p) as h:
+        for i in range(reps + 1):
+            st.copy_(fresh)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            h.sw_run(st, steps)
+            b.record()
+            b.synchronize()
+            if i:
+                ts.append(a.elapsed_time(b) / 1e3)
+        rc = h.sw_sync_status()
+        if rc < 0:
+            raise S.SweptError(rc, "launch_map")
+    return min(ts)
+
+
+def run_map(scheme: str, precision: int, exps, widths, target: float, cap: int, reps: int, emit=print):
+    best = []
+    for e in exps:
+        n = 1 << e
+        ws = [W for W in widths if n % W == 0 and n >= 2 * W]
+        steps = steps_for(scheme, n, target, max(ws), cap)
+        row = {}
+        for W in ws:
+            t = measure(scheme, precision, n, S.SW_SWEPT, W, steps, reps)
+            row[W] = t
+            emit(json.dumps({"kind": "point", "scheme": scheme, "precision": precision, "n": n, "method": "swept",
+                             "W": W, "steps": steps, "us_per_step": t / steps * 1e6,
+                             "gcell_steps_per_s": n * steps / t / 1e9}))
+        tc = measure(scheme, precision, n, S.SW_PERSTEP, 0, steps, reps)
+        emit(json.dumps({"kind": "point", "scheme": scheme, "precision": precision, "n": n, "method": "perstep",
+                         "W": None, "steps": steps, "us_per_step": tc / steps * 1e6,
+                         "gcell_steps_per_s": n * steps / tc / 1e9}))
+        wb = min(row, key=row.get)
+        best.append((n, row[wb] / steps * 1e6))
+        emit(json.dumps({"kind": "best", "scheme": scheme, "precision": precision, "n": n, "W": wb,
+                         "swept_us_per_step": row[wb] / steps * 1e6, "perstep_us_per_step": tc / steps * 1e6,
+                         "speedup": tc / row[wb]}))
+    A, b, r2 = power_fit([n for n, _ in best], [y for _, y in best])
+    emit(json.dumps({"kind": "fit", "scheme": scheme, "precision": precision, "A_us": A, "b": b, "r2": r2,
+                     "n_range": [best[0][0], best[-1][0]]}))
+    return best, (A, b, r2)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--scheme", choices=("heat", "euler"), default="heat")
+    ap.add_argument("--precision", choices=tuple(PREC), default="fp64")
+    ap.add_argument("--exps", type=int, nargs=2, default=(14, 24), help="log2 N range, inclusive")
+    ap.add_argument("--step", type=int, default=1, help="log2 N stride")
+    ap.add_argument("--widths", type=int, nargs="+", default=(32, 64, 128, 256, 512, 1024))
+    ap.add_argument("--target", type=float, default=None, help="cell-steps per measurement")
+    ap.add_argument("--cap", type=int, default=20000, help="most time steps per measurement")
+    ap.add_argument("--reps", type=int, default=2)
+    a = ap.parse_args(argv)
+    import torch
+    from . import build
+    build.build()
+    torch.cuda.set_device(0)
+    target = a.target if a.target is not None else (2.0 ** 32 if a.scheme == "heat" else 2.0 ** 28)
+    run_map(a.scheme, PREC[a.precision], range(a.exps[0], a.exps[1] + 1, a.step), a.widths, target, a.cap, a.reps)
+
+
+if __name__ == "__main__":
+    main()
