@@ -82,6 +82,14 @@ extern "C" {
 /* sw_problem.flags */
 #define SW_FLAG_GENERIC 1  /* swept: use the generic shared-memory phase kernel for every
                               phase (no register-resident Diamond kernel); same results */
+#define SW_FLAG_EULER_FOLD 2 /* swept Euler: run every phase with a complete (or no) upper
+                                half on the register-resident kernel where it is instantiated
+                                (W = 128; FP32 forms also W = 256), otherwise as without the
+                                flag; same results. Off by default: on GB300 it measured
+                                slower than the generic kernel, because the scheme is bound by
+                                arithmetic and the folded kernel evaluates K + 1 faces per K
+                                cells per level at a lower occupancy. Ignored with
+                                SW_FLAG_GENERIC. */
 
 #define SW_MIN_TILE 4
 #define SW_MAX_TILE 1024
@@ -99,7 +107,7 @@ typedef struct sw_problem {
     double gamma;       /* Euler: ratio of specific heats (> 1) */
     int32_t tile_width; /* swept base width W: even, SW_MIN_TILE..SW_MAX_TILE,
                            divides n; 0 selects the library default */
-    int32_t flags;      /* 0 or SW_FLAG_GENERIC (sw_run_noalloc: must be 0) */
+    int32_t flags;      /* 0 or SW_FLAG_GENERIC | SW_FLAG_EULER_FOLD (sw_run_noalloc: must be 0) */
 } sw_problem;
 
 typedef struct sw_handle sw_handle;

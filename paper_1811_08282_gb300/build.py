@@ -20,7 +20,7 @@ LIB = os.path.join(OUT_DIR, "libswept.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + os.path.join(ROOT, "include")]
-TUS = ["api.cu", "noalloc.cu", "fold.cu", "batch.cu"]
+TUS = ["api.cu", "noalloc.cu", "fold.cu", "fold_euler.cu", "batch.cu"]
 
 
 def _nvcc() -> str:

@@ -65,7 +65,7 @@ int validate(const sw_problem *p) {
     if (p->precision < SW_FP64 || p->precision > SW_FP32_COMP) return SW_ERR_BAD_ARG;
     if (p->boundary != SW_PERIODIC && p->boundary != SW_TRANSMISSIVE) return SW_ERR_BAD_ARG;
     if (p->method != SW_SWEPT && p->method != SW_PERSTEP) return SW_ERR_BAD_ARG;
-    if (p->flags & ~SW_FLAG_GENERIC) return SW_ERR_BAD_ARG;
+    if (p->flags & ~(SW_FLAG_GENERIC | SW_FLAG_EULER_FOLD)) return SW_ERR_BAD_ARG;
     if (p->n < 4 || p->n > (int64_t(1) << 40)) return SW_ERR_BAD_ARG;
     if (p->scheme == SW_HEAT) {
         if (!(p->r > 0.0) || !(p->r < 1e6)) return SW_ERR_BAD_ARG;
@@ -140,6 +140,11 @@ int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st) {
     const bool fold = std::is_same<typename P::Params, HeatParams>::value && periodic &&
                       !(h->prob.flags & SW_FLAG_GENERIC) && fold_supported(h->prob.precision, W);
     const int64_t fold_warps = int64_t(h->sms) * fold_warps_per_sm(h->prob.precision, W);
+    // Euler at W = 128 (and 256 in FP32), on request only (it is the slower kernel on GB300)
+    const bool efold = std::is_same<typename P::Params, EulerParams>::value &&
+                       (h->prob.flags & SW_FLAG_EULER_FOLD) && !(h->prob.flags & SW_FLAG_GENERIC) &&
+                       euler_fold_supported(h->prob.precision, W);
+    const int64_t efold_warps = int64_t(h->sms) * euler_fold_warps_per_sm(h->prob.precision, W);
     int64_t launches = 0;
     for (int64_t p = 0; p <= P_last; ++p) {
         PhaseArgs<T> a{};
@@ -168,6 +173,11 @@ int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st) {
             FoldPhase ph{a.p, a.n, h->M, h->S, a.lower, a.upper, a.write_lower, a.write_upper,
                          a.flank_in, a.flank_out, state};
             cudaError_t e = launch_fold(h->prob.precision, W, ph, h->hp, fold_warps, st);
+            if (e != cudaSuccess) return cuda_status(e);
+        } else if (efold && !a.write_upper) {
+            EulerFoldPhase ph{a.p, a.periodic, a.n, h->M, a.nstruct, h->S, a.lower, a.upper, a.write_lower,
+                              a.flank_in, a.flank_out, state};
+            cudaError_t e = launch_euler_fold(h->prob.precision, W, ph, h->ep, efold_warps, st);
             if (e != cudaSuccess) return cuda_status(e);
         } else {
             k_swept_phase<P><<<(unsigned)a.nstruct, h->threads, h->smem, st>>>(a, prm);

@@ -1,8 +1,10 @@
-// fold.h -- host launcher of the register-resident heat Diamond kernel (fold.cu).
+// fold.h -- host launchers of the register-resident phase kernels: heat (fold.cu)
+// and Euler (fold_euler.cu).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "euler.cuh"
 #include "heat.cuh"
 
 namespace sw {
@@ -29,5 +31,25 @@ cudaError_t launch_fold(int precision, int W, const FoldPhase &ph, const HeatPar
 
 // Warps per SM the launcher aims for at this precision / width (register bound).
 int fold_warps_per_sm(int precision, int W);
+
+// Euler: true when k_euler_fold has an instantiation (FP64: W = 128; FP32 and
+// FP32 hi/lo: W = 128, 256).
+bool euler_fold_supported(int precision, int W);
+
+// One phase of an Euler problem, periodic or transmissive, whose upper half is
+// complete (or absent): nstruct structures (transmissive seam-centred phases have
+// M + 1, the two at the domain ends half outside it). Flanks in the k_swept_phase
+// layout with the fields of the Euler policies.
+struct EulerFoldPhase {
+    int p, periodic;
+    int64_t n, M, nstruct, S;
+    int lower, upper, write_lower;
+    const void *flank_in;
+    void *flank_out;
+    void *state;
+};
+cudaError_t launch_euler_fold(int precision, int W, const EulerFoldPhase &ph, const EulerParams &prm, int64_t warps,
+                              cudaStream_t st);
+int euler_fold_warps_per_sm(int precision, int W);
 
 }  // namespace sw

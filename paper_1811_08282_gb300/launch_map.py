@@ -92,7 +92,10 @@ def measure(scheme: str, precision: int, n: int, method: int, W: int, steps: int
     return min(ts)
 
 
-def run_map(scheme: str, precision: int, exps, widths, target: float, cap: int, reps: int, emit=print):
+def run_map(scheme: str, precision: int, exps, widths, target: float, cap: int, reps: int, emit=print,
+            fit_exps=None):
+    """Measure every (N, W) and per-step per N; fit the best swept time per step over
+    N in 2^fit_exps[0] .. 2^fit_exps[1] (default: every measured N)."""
     best = []
     for e in exps:
         n = 1 << e
@@ -114,9 +117,11 @@ def run_map(scheme: str, precision: int, exps, widths, target: float, cap: int, 
         emit(json.dumps({"kind": "best", "scheme": scheme, "precision": precision, "n": n, "W": wb,
                          "swept_us_per_step": row[wb] / steps * 1e6, "perstep_us_per_step": tc / steps * 1e6,
                          "speedup": tc / row[wb]}))
-    A, b, r2 = power_fit([n for n, _ in best], [y for _, y in best])
+    lo, hi = fit_exps if fit_exps else (0, 62)
+    pts = [(n, y) for n, y in best if (1 << lo) <= n <= (1 << hi)]
+    A, b, r2 = power_fit([n for n, _ in pts], [y for _, y in pts])
     emit(json.dumps({"kind": "fit", "scheme": scheme, "precision": precision, "A_us": A, "b": b, "r2": r2,
-                     "n_range": [best[0][0], best[-1][0]]}))
+                     "n_range": [pts[0][0], pts[-1][0]]}))
     return best, (A, b, r2)
 
 
@@ -130,13 +135,16 @@ def main(argv=None):
     ap.add_argument("--target", type=float, default=None, help="cell-steps per measurement")
     ap.add_argument("--cap", type=int, default=20000, help="most time steps per measurement")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--fit-exps", type=int, nargs=2, default=None,
+                    help="log2 N range of the power-law fit (default: all measured)")
     a = ap.parse_args(argv)
     import torch
     from . import build
     build.build()
     torch.cuda.set_device(0)
     target = a.target if a.target is not None else (2.0 ** 32 if a.scheme == "heat" else 2.0 ** 28)
-    run_map(a.scheme, PREC[a.precision], range(a.exps[0], a.exps[1] + 1, a.step), a.widths, target, a.cap, a.reps)
+    run_map(a.scheme, PREC[a.precision], range(a.exps[0], a.exps[1] + 1, a.step), a.widths, target, a.cap, a.reps,
+            fit_exps=a.fit_exps)
 
 
 if __name__ == "__main__":

@@ -1,7 +1,7 @@
 """Run one configured case through the C ABI (for profilers and quick timing).
 
     python -m paper_1811_08282_gb300.profile_case --scheme heat --precision fp64 \
-        --method swept --n 16777216 --steps 2048 --width 1024 [--repeat 1]
+        --method swept --n 16777216 --steps 2048 --width 1024 [--repeat 1] [--generic]
 
 Inputs are the seeded synthetic states of ``inputs`` (heat: 32 sine modes;
 Euler: Sod, or 64 random Riemann segments with --init riemann). Prints the
@@ -30,6 +30,7 @@ def main(argv=None):
     ap.add_argument("--width", type=int, default=1024)
     ap.add_argument("--r", type=float, default=0.3)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--generic", action="store_true", help="force the generic phase kernel (SW_FLAG_GENERIC)")
     a = ap.parse_args(argv)
 
     import torch
@@ -41,7 +42,8 @@ def main(argv=None):
                   boundary=S.SW_PERIODIC if bc == "periodic" else S.SW_TRANSMISSIVE,
                   method=S.SW_SWEPT if a.method == "swept" else S.SW_PERSTEP, n=a.n, r=a.r,
                   dt_dx=(I.sod_lambda() if a.init == "sod" else I.riemann_lambda()), gamma=I.GAMMA,
-                  tile_width=a.width if a.method == "swept" else 0)
+                  tile_width=a.width if a.method == "swept" else 0,
+                  flags=S.SW_FLAG_GENERIC if a.generic else 0)
     if heat:
         x = I.heat_initial(I.heat_modes(a.n, 32, seed=1))
     elif a.init == "sod":
@@ -64,7 +66,7 @@ def main(argv=None):
         launches = h.sw_last_launch_count()
         rc = h.sw_sync_status()
     print(json.dumps({"scheme": a.scheme, "precision": a.precision, "method": a.method, "n": a.n,
-                      "steps": a.steps, "width": a.width, "launches": launches, "seconds": t,
+                      "steps": a.steps, "width": a.width, "generic": a.generic, "launches": launches, "seconds": t,
                       "gcell_updates_per_s": a.n * a.steps / t / 1e9, "status": rc}))
     return 0 if rc == 0 else 1
 

@@ -26,6 +26,7 @@ SW_ERR_TOO_LARGE = -7
 SW_NOALLOC_SCRATCH_BYTES = 16 << 20
 SW_MIN_TILE, SW_MAX_TILE = 4, 1024
 SW_FLAG_GENERIC = 1
+SW_FLAG_EULER_FOLD = 2
 
 # every symbol declared in include/swept.h
 EXPORTS = (

@@ -66,7 +66,7 @@ def test_state_layout(lib, scheme, prec, planes, esize):
     dict(n=4096, precision=3),
     dict(n=4096, boundary=2),
     dict(n=4096, method=5),
-    dict(n=4096, flags=2),                   # unknown flag bit
+    dict(n=4096, flags=4),                   # unknown flag bit
     dict(n=2),
     dict(n=4096, scheme=S.SW_EULER, dt_dx=0.0),
     dict(n=4096, scheme=S.SW_EULER, dt_dx=0.1, gamma=1.0),
