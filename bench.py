@@ -398,6 +398,41 @@ def run_ours(args):
                                           "note": "sw_conservation call incl. read-back of the sum"}
     del stc
 
+    # hybrid CPU/GPU split (Section 4.2, Eq. 1): the host cores take 1 / (1 + WF / threads) of
+    # the tiles; short sweep of the work factor, then the best against the GPU alone (same steps)
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    ph = problem(S.SW_FP64, S.SW_SWEPT, best_w)
+    sth = S.to_state(ph, u0_dev)
+    hy_steps = 2048
+    with S.Handle(ph) as hh:
+        def hyb(wf, steps):
+            sth.copy_(u0_dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hh.sw_run_hybrid(sth, steps, wf, threads, stream)
+            return time.perf_counter() - t0
+        wf_rates = {}
+        for wf in (16, 32, 48, 64, 96, 128, 192, 256):
+            try:
+                hyb(wf, 64)
+                wf_rates[wf] = N * hy_steps / hyb(wf, hy_steps) / 1e9
+            except S.SweptError:
+                pass
+        best_wf = max(wf_rates, key=wf_rates.get)
+        t_h = min(hyb(best_wf, 4 * hy_steps) for _ in range(2))
+        hyb_state = sth.clone()
+        sth.copy_(u0_dev)
+        hh.sw_run(sth, 4 * hy_steps, stream)
+        torch.cuda.synchronize()
+        t_g = timed_run(hh, sth, 4 * hy_steps, u0_dev)
+        same = bool(torch.equal(hyb_state, sth))
+    gt, per_thread = S.sw_hybrid_split(N // best_w, best_wf, threads)
+    compare["hybrid_fp64"] = {"value": N * 4 * hy_steps / t_h / 1e9, "gpu_only": N * 4 * hy_steps / t_g / 1e9,
+                              "speedup": t_g / t_h, "steps": 4 * hy_steps, "W": best_w, "threads": threads,
+                              "work_factor": best_wf, "gpu_tiles": gt, "host_tiles": per_thread * threads,
+                              "wf_sweep": wf_rates, "bitwise_equal_to_gpu_only": same}
+    del sth, hyb_state
+
     perstep_bytes = 16  # FP64 per-step: read + write one value per update
     compare["fp64_perstep"]["hbm_gbs"] = compare["fp64_perstep"]["value"] * perstep_bytes
     compare["speedup_swept_over_perstep_fp64"] = compare["fp64_swept"]["value"] / compare["fp64_perstep"]["value"]

@@ -139,6 +139,33 @@ SW_API int sw_run(sw_handle *h, void *state, int64_t nsteps, void *stream);
 SW_API int sw_run_host(sw_handle *h, const void *state_in, void *state_out, int64_t nsteps,
                 void *stream);
 
+/* The affinity split of Section 4.2 (Eq. 1, the GPU work factor WF = N_GPU / N_CPU,
+ * counted in tiles): for `tiles` tiles, `cpu_threads` host threads each take
+ * tiles_per_thread = floor(tiles / (work_factor + cpu_threads)) tiles and the GPU
+ * the rest (gpu_tiles >= work_factor * tiles_per_thread). Pure host arithmetic.
+ * Errors: SW_ERR_BAD_ARG when tiles < 2, work_factor < 1, cpu_threads outside
+ * 1..4096 or tiles_per_thread would be 0. Output pointers may be NULL. */
+SW_API int sw_hybrid_split(int64_t tiles, int32_t work_factor, int32_t cpu_threads, int64_t *gpu_tiles,
+                           int64_t *tiles_per_thread);
+
+/* Swept run shared between the GPU and `cpu_threads` host threads (Section 4.2's
+ * heterogeneous decomposition, the split of sw_hybrid_split): in every phase the GPU
+ * runs structures 0 .. gpu_tiles-1 and the host threads the rest, concurrently; the
+ * host threads work on pinned host mirrors of the flank buffers and of the state,
+ * and once per phase the one or two flank slots at the GPU/host boundaries cross
+ * between device and host memory on `stream`. The host threads evaluate the same
+ * per-cell arithmetic with the host's IEEE operations (no contraction), so the
+ * result is bitwise that of sw_run. `state` is the device state (in place): the
+ * host's tiles are read from it at the start and written back at the end.
+ * Synchronous: returns when the run is complete. The first call allocates the host
+ * mirrors (2 x the flank scratch + one state, pinned) and starts the threads; both
+ * are kept by the handle until sw_destroy (a call with another thread count restarts
+ * the threads). Not safe to call concurrently on one handle.
+ * Errors: SW_ERR_BAD_ARG (method not swept, the split above, NULL state, nsteps < 0),
+ * SW_ERR_OOM, SW_ERR_CUDA. */
+SW_API int sw_run_hybrid(sw_handle *h, void *state, int64_t nsteps, int32_t work_factor, int32_t cpu_threads,
+                         void *stream);
+
 /* Conversions between FP64 planes (nplanes_fp64 = 1 heat, 3 Euler, each n
  * doubles) and the working layout of `p`, on the device. FP32: round to
  * nearest; FP32_COMP: hi = float(x), lo = float(x - hi). */

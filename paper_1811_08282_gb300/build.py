@@ -18,8 +18,10 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libswept.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code is compiled without floating-point contraction: the host share of a hybrid run
+# must round every operation exactly as the device kernels do
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-         "-I" + os.path.join(ROOT, "include")]
+         "-Xcompiler", "-ffp-contract=off", "-I" + os.path.join(ROOT, "include")]
 TUS = ["api.cu", "noalloc.cu", "fold.cu", "fold_euler.cu", "batch.cu"]
 
 
@@ -64,7 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(TUS)) as ex:
         objs = list(ex.map(compile_one, TUS))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -6,18 +6,85 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/swept.h"
+#include "cpu_phase.h"
 #include "fold.h"
 #include "perstep.cuh"
 #include "schemes.cuh"
 #include "swept_phase.cuh"
 
 using namespace sw;
+
+namespace {
+
+// Persistent host threads for the host share of a hybrid run: run(f) calls f(t) for
+// t = 0 .. size-1, t = 0 on the calling thread, and returns when all calls have.
+class HostPool {
+   public:
+    explicit HostPool(int n) : n_(n) {
+        for (int t = 1; t < n; ++t) th_.emplace_back([this, t] { loop(t); });
+    }
+    ~HostPool() {
+        {
+            std::lock_guard<std::mutex> g(m_);
+            stop_ = true;
+            ++gen_;
+        }
+        cv_.notify_all();
+        for (auto &t : th_) t.join();
+    }
+    int size() const { return n_; }
+    void run(const std::function<void(int)> &f) {
+        {
+            std::lock_guard<std::mutex> g(m_);
+            job_ = &f;
+            pending_ = n_ - 1;
+            ++gen_;
+        }
+        cv_.notify_all();
+        f(0);
+        std::unique_lock<std::mutex> lk(m_);
+        done_.wait(lk, [&] { return pending_ == 0; });
+        job_ = nullptr;
+    }
+
+   private:
+    void loop(int t) {
+        int64_t seen = 0;
+        for (;;) {
+            const std::function<void(int)> *job;
+            {
+                std::unique_lock<std::mutex> lk(m_);
+                cv_.wait(lk, [&] { return gen_ != seen; });
+                seen = gen_;
+                if (stop_) return;
+                job = job_;
+            }
+            (*job)(t);
+            std::lock_guard<std::mutex> g(m_);
+            if (--pending_ == 0) done_.notify_one();
+        }
+    }
+    int n_;
+    std::vector<std::thread> th_;
+    std::mutex m_;
+    std::condition_variable cv_, done_;
+    const std::function<void(int)> *job_ = nullptr;
+    int64_t gen_ = 0;
+    int pending_ = 0;
+    bool stop_ = false;
+};
+
+}  // namespace
 
 struct sw_handle {
     sw_problem prob;
@@ -43,6 +110,11 @@ struct sw_handle {
     std::vector<int32_t> kinds;
     int64_t ev_cap = 0, ev_used = 0;
     int sms = 152;  // streaming multiprocessors of the device
+    // hybrid runs: pinned host mirrors of the flank buffers and the state, host threads
+    void *h_flank[2] = {nullptr, nullptr};
+    void *h_state = nullptr;
+    HostPool *pool = nullptr;
+    cudaEvent_t hy_ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -129,8 +201,64 @@ inline void trace_end(sw_handle *h, int64_t i, cudaStream_t st) {
     }
 }
 
+// Host scheme matching each GPU storage policy (same fields, same per-cell arithmetic).
+template <class P> struct HostOf;
+template <> struct HostOf<HeatPolicy<0>> {
+    using type = HostHeatPlain<HostOpsD>;
+    static type make(const sw_handle *h) { return type{h->hp.r}; }
+};
+template <> struct HostOf<HeatPolicy<1>> {
+    using type = HostHeatPlain<HostOpsF>;
+    static type make(const sw_handle *h) { return type{h->hp.rf}; }
+};
+template <> struct HostOf<HeatPolicy<2>> {
+    using type = HostHeatComp;
+    static type make(const sw_handle *h) { return type{h->hp.rf, h->hp.rf_lo}; }
+};
+template <> struct HostOf<EulerPolicy<0>> {
+    using type = HostEuler<HostOpsD, false>;
+    static type make(const sw_handle *h) { return type{eu_k<HostOpsD>(h->ep), {}}; }
+};
+template <> struct HostOf<EulerPolicy<1>> {
+    using type = HostEuler<HostOpsF, false>;
+    static type make(const sw_handle *h) { return type{eu_k<HostOpsF>(h->ep), {}}; }
+};
+template <> struct HostOf<EulerPolicyComp> {
+    using type = HostEuler<HostOpsF, true>;
+    static type make(const sw_handle *h) { return type{eu_k<HostOpsF>(h->ep), {}}; }
+};
+
+// A hybrid run (Section 4.2's affinity split): the GPU runs structures 0 .. Mg-1 of every
+// phase, the host threads the rest.
+struct Hybrid {
+    int64_t Mg;
+    int64_t first = INT64_MAX, last = -1;  // state cells the host wrote
+};
+
+// Copy the flank slot of structure b (all fields, both sides) between the device and its
+// pinned host mirror.
+cudaError_t copy_slot(sw_handle *h, int buf, int64_t b, bool to_device, cudaStream_t st) {
+    const size_t es = h->esize;
+    const size_t pitch = size_t(h->S) * 2 * h->W * es, width = size_t(2) * h->W * es;
+    const size_t off = size_t(b) * 2 * h->W * es;
+    char *dv = static_cast<char *>(h->flank[buf]) + off;
+    char *hv = static_cast<char *>(h->h_flank[buf]) + off;
+    return to_device ? cudaMemcpy2DAsync(dv, pitch, hv, pitch, width, h->nsnap, cudaMemcpyHostToDevice, st)
+                     : cudaMemcpy2DAsync(hv, pitch, dv, pitch, width, h->nsnap, cudaMemcpyDeviceToHost, st);
+}
+
+// Copy state cells [j0, j1] of every plane between the device state and the host mirror.
+cudaError_t copy_cells(sw_handle *h, void *state, int64_t j0, int64_t j1, bool to_device, cudaStream_t st) {
+    if (j1 < j0) return cudaSuccess;
+    const size_t es = h->esize, pitch = size_t(h->prob.n) * es, width = size_t(j1 - j0 + 1) * es;
+    char *dv = static_cast<char *>(state) + size_t(j0) * es;
+    char *hv = static_cast<char *>(h->h_state) + size_t(j0) * es;
+    return to_device ? cudaMemcpy2DAsync(dv, pitch, hv, pitch, width, h->nio, cudaMemcpyHostToDevice, st)
+                     : cudaMemcpy2DAsync(hv, pitch, dv, pitch, width, h->nio, cudaMemcpyDeviceToHost, st);
+}
+
 template <class P>
-int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st) {
+int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st, Hybrid *hy = nullptr) {
     using T = typename P::T;
     const int H = h->H, W = h->W;
     const int64_t P_last = (L + H - 1) / H;
@@ -146,6 +274,20 @@ int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st) {
                        euler_fold_supported(h->prob.precision, W);
     const int64_t efold_warps = int64_t(h->sms) * euler_fold_warps_per_sm(h->prob.precision, W);
     int64_t launches = 0;
+    using Sch = typename HostOf<P>::type;
+    std::vector<Sch> sch;
+    std::vector<std::vector<T>> work;
+    std::vector<WrittenRange> written;
+    if (hy) {
+        const int nt = h->pool->size();
+        for (int t = 0; t < nt; ++t) sch.push_back(HostOf<P>::make(h));
+        work.assign(nt, std::vector<T>(size_t(2) * Sch::NF * (W + 2)));
+        written.assign(nt, WrittenRange{});
+        // the host's tiles of the initial state
+        cudaError_t e = copy_cells(h, state, hy->Mg * W, h->prob.n - 1, false, st);
+        if (e == cudaSuccess) e = cudaEventRecord(h->hy_ev[1], st);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
     for (int64_t p = 0; p <= P_last; ++p) {
         PhaseArgs<T> a{};
         a.n = h->prob.n;
@@ -168,9 +310,20 @@ int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st) {
         typename P::Params prm;
         if constexpr (std::is_same<typename P::Params, HeatParams>::value) prm = h->hp;
         else prm = h->ep;
+        const int64_t nstruct = a.nstruct;
+        if (hy) {
+            // the host's flank slot of phase p-1 that a GPU structure of phase p reads: the
+            // seam structure Mg (p even), or the last tile M-1 across the periodic wrap (p odd)
+            const int64_t slot = (p == 0) ? -1 : ((p & 1) == 0 ? hy->Mg : (periodic ? h->M - 1 : -1));
+            if (slot >= 0) {
+                cudaError_t e = copy_slot(h, (int)((p - 1) & 1), slot, true, st);
+                if (e != cudaSuccess) return cuda_status(e);
+            }
+            a.nstruct = hy->Mg;
+        }
         trace_begin(h, launches, p == 0 ? 0 : (p == P_last ? 2 : 1), st);
         if (fold && !a.write_upper) {
-            FoldPhase ph{a.p, a.n, h->M, h->S, a.lower, a.upper, a.write_lower, a.write_upper,
+            FoldPhase ph{a.p, a.n, h->M, h->S, a.nstruct, a.lower, a.upper, a.write_lower, a.write_upper,
                          a.flank_in, a.flank_out, state};
             cudaError_t e = launch_fold(h->prob.precision, W, ph, h->hp, fold_warps, st);
             if (e != cudaSuccess) return cuda_status(e);
@@ -184,8 +337,38 @@ int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st) {
         }
         trace_end(h, launches, st);
         ++launches;
+        if (hy) {
+            // the GPU's flank slot of phase p that a host structure of phase p+1 reads: the
+            // last GPU tile Mg-1 (p even), or the seam structure 0 across the periodic wrap (p odd)
+            const int64_t slot = (p == P_last) ? -1 : ((p & 1) == 0 ? hy->Mg - 1 : (periodic ? 0 : -1));
+            cudaError_t e = cudaSuccess;
+            if (slot >= 0) e = copy_slot(h, (int)(p & 1), slot, false, st);
+            if (e == cudaSuccess) e = cudaEventRecord(h->hy_ev[p & 1], st);
+            // the host's structures of phase p, once the GPU's slots of phase p-1 have arrived
+            if (e == cudaSuccess) e = cudaEventSynchronize(h->hy_ev[(p + 1) & 1]);
+            if (e != cudaSuccess) return cuda_status(e);
+            HostPhase<T> hp{a.n, W, H, a.periodic, a.p, a.F, a.lower, a.upper, a.write_lower, a.write_upper,
+                            h->M, h->S,
+                            p == 0 ? nullptr : static_cast<const T *>(h->h_flank[(p - 1) & 1]),
+                            static_cast<T *>(h->h_flank[p & 1]), static_cast<T *>(h->h_state)};
+            const int64_t b0 = hy->Mg, cnt = nstruct - hy->Mg;
+            const int nt = h->pool->size();
+            h->pool->run([&](int t) {
+                const int64_t lo = b0 + cnt * t / nt, hi = b0 + cnt * (t + 1) / nt;
+                for (int64_t b = lo; b < hi; ++b) cpu_structure(sch[t], hp, b, work[t].data(), written[t]);
+            });
+        }
     }
     h->last_launches = launches;
+    if (hy) {
+        for (const WrittenRange &w : written) {
+            hy->first = std::min(hy->first, w.first);
+            hy->last = std::max(hy->last, w.last);
+        }
+        cudaError_t e = copy_cells(h, state, hy->first, hy->last, true, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
     return cuda_status(cudaGetLastError());
 }
 
@@ -480,6 +663,12 @@ void sw_destroy(sw_handle *h) {
     cudaFree(h->d_status);
     cudaFree(h->d_partial);
     cudaFree(h->d_sums);
+    cudaFreeHost(h->h_flank[0]);
+    cudaFreeHost(h->h_flank[1]);
+    cudaFreeHost(h->h_state);
+    for (cudaEvent_t e : h->hy_ev)
+        if (e) cudaEventDestroy(e);
+    delete h->pool;
     delete h;
 }
 
@@ -541,6 +730,59 @@ int sw_run(sw_handle *h, void *state, int64_t nsteps, void *stream) {
     case SW_FP64: return launch_perstep_euler_t<OpsD, false>(h, state, nsteps, st);
     case SW_FP32: return launch_perstep_euler_t<OpsF, false>(h, state, nsteps, st);
     default: return launch_perstep_euler_t<OpsF, true>(h, state, nsteps, st);
+    }
+}
+
+int sw_hybrid_split(int64_t tiles, int32_t work_factor, int32_t cpu_threads, int64_t *gpu_tiles,
+                    int64_t *tiles_per_thread) {
+    if (tiles < 2 || work_factor < 1 || cpu_threads < 1 || cpu_threads > 4096) return SW_ERR_BAD_ARG;
+    // Eq. 1: the GPU takes work_factor times the tiles of one host thread
+    const int64_t per = tiles / (int64_t(work_factor) + cpu_threads);
+    if (per < 1) return SW_ERR_BAD_ARG;
+    const int64_t g = tiles - per * cpu_threads;
+    if (gpu_tiles) *gpu_tiles = g;
+    if (tiles_per_thread) *tiles_per_thread = per;
+    return SW_OK;
+}
+
+int sw_run_hybrid(sw_handle *h, void *state, int64_t nsteps, int32_t work_factor, int32_t cpu_threads,
+                  void *stream) {
+    if (!h || !state || nsteps < 0) return SW_ERR_BAD_ARG;
+    if (h->prob.method != SW_SWEPT) return SW_ERR_BAD_ARG;
+    int64_t Mg = 0;
+    int rc = sw_hybrid_split(h->M, work_factor, cpu_threads, &Mg, nullptr);
+    if (rc != SW_OK) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    h->last_launches = 0;
+    h->ev_used = 0;
+    if (nsteps == 0) return SW_OK;
+    if (!h->h_state) {
+        cudaError_t e = cudaHostAlloc(&h->h_flank[0], h->flank_bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaHostAlloc(&h->h_flank[1], h->flank_bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaHostAlloc(&h->h_state, size_t(h->nio) * h->prob.n * h->esize, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->hy_ev[0], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->hy_ev[1], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (!h->pool || h->pool->size() != cpu_threads) {
+        delete h->pool;
+        h->pool = new (std::nothrow) HostPool(cpu_threads);
+        if (!h->pool) return SW_ERR_OOM;
+    }
+    Hybrid hy{Mg};
+    const sw_problem &p = h->prob;
+    const int64_t L = nsteps * (p.scheme == SW_HEAT ? 1 : 4);
+    if (p.scheme == SW_HEAT) {
+        switch (p.precision) {
+        case SW_FP64: return launch_swept<HeatPolicy<0>>(h, state, L, st, &hy);
+        case SW_FP32: return launch_swept<HeatPolicy<1>>(h, state, L, st, &hy);
+        default: return launch_swept<HeatPolicy<2>>(h, state, L, st, &hy);
+        }
+    }
+    switch (p.precision) {
+    case SW_FP64: return launch_swept<EulerPolicy<0>>(h, state, L, st, &hy);
+    case SW_FP32: return launch_swept<EulerPolicy<1>>(h, state, L, st, &hy);
+    default: return launch_swept<EulerPolicyComp>(h, state, L, st, &hy);
     }
 }
 

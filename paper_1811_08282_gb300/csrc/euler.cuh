@@ -28,16 +28,18 @@ template <class O> struct EulerK {
     T gamma, gm1, lam, hlam;
 };
 
+#pragma nv_exec_check_disable
 template <class O>
-__device__ __forceinline__ typename O::T eu_pressure(const EulerK<O> &k, typename O::T rho, typename O::T m,
+SW_HD typename O::T eu_pressure(const EulerK<O> &k, typename O::T rho, typename O::T m,
                                                      typename O::T E) {
     using T = typename O::T;
     T u = O::div(m, rho);
     return O::mul(k.gm1, O::sub(E, O::mul(O::mul(T(0.5), m), u)));
 }
 
+#pragma nv_exec_check_disable
 template <class O>
-__device__ __forceinline__ typename O::T eu_ratio(typename O::T pm, typename O::T p0, typename O::T pp) {
+SW_HD typename O::T eu_ratio(typename O::T pm, typename O::T p0, typename O::T pp) {
     using T = typename O::T;
     T dm = O::sub(p0, pm);
     T dp = O::sub(pp, p0);
@@ -45,8 +47,9 @@ __device__ __forceinline__ typename O::T eu_ratio(typename O::T pm, typename O::
     return T(0);
 }
 
+#pragma nv_exec_check_disable
 template <class O>
-__device__ __forceinline__ void eu_phys_flux(const EulerK<O> &k, typename O::T rho, typename O::T m,
+SW_HD void eu_phys_flux(const EulerK<O> &k, typename O::T rho, typename O::T m,
                                              typename O::T E, typename O::T &f0, typename O::T &f1,
                                              typename O::T &f2, typename O::T &speed) {
     using T = typename O::T;
@@ -60,8 +63,9 @@ __device__ __forceinline__ void eu_phys_flux(const EulerK<O> &k, typename O::T r
 }
 
 // Numerical flux at the face between cell a (left) and cell b (right).
+#pragma nv_exec_check_disable
 template <class O>
-__device__ __forceinline__ void eu_face_flux(const EulerK<O> &k, typename O::T a0, typename O::T a1,
+SW_HD void eu_face_flux(const EulerK<O> &k, typename O::T a0, typename O::T a1,
                                              typename O::T a2, typename O::T tha, typename O::T b0,
                                              typename O::T b1, typename O::T b2, typename O::T thb,
                                              typename O::T &o0, typename O::T &o1, typename O::T &o2) {
@@ -82,12 +86,35 @@ __device__ __forceinline__ void eu_face_flux(const EulerK<O> &k, typename O::T a
     o2 = O::sub(O::mul(T(0.5), O::add(fl2, fr2)), O::mul(hs, O::sub(r2, l2)));
 }
 
-template <class O> __device__ __forceinline__ EulerK<O> eu_k(const EulerParams &p);
-template <> __device__ __forceinline__ EulerK<OpsD> eu_k<OpsD>(const EulerParams &p) {
-    return EulerK<OpsD>{p.gamma, p.gm1, p.lam, p.hlam};
+#pragma nv_exec_check_disable
+template <class O>
+SW_HD EulerK<O> eu_k(const EulerParams &p) {
+    if constexpr (std::is_same<typename O::T, double>::value) return EulerK<O>{p.gamma, p.gm1, p.lam, p.hlam};
+    else return EulerK<O>{p.gammaf, p.gm1f, p.lamf, p.hlamf};
 }
-template <> __device__ __forceinline__ EulerK<OpsF> eu_k<OpsF>(const EulerParams &p) {
-    return EulerK<OpsF>{p.gammaf, p.gm1f, p.lamf, p.hlamf};
+
+// State updates of the two flux sub-steps, shared by every kernel and the host:
+// plain forms Q - c dF; hi/lo form: predictor Q* = h + (l - (lambda/2) dF) in FP32,
+// final (h, l) + (-lambda dF) with TwoSum / Fast2Sum.
+#pragma nv_exec_check_disable
+template <class O>
+SW_HD typename O::T eu_update(typename O::T q, typename O::T c, typename O::T d) {
+    return O::sub(q, O::mul(c, d));
+}
+
+#pragma nv_exec_check_disable
+template <class O>
+SW_HD float eu_comp_predict(float h, float l, float hlam, float d) {
+    return O::add(h, O::sub(l, O::mul(hlam, d)));
+}
+
+#pragma nv_exec_check_disable
+template <class O>
+SW_HD void eu_comp_final(float h, float l, float lam, float d, float &nh, float &nl) {
+    const float delta = -O::mul(lam, d);
+    float sm, e;
+    two_sum_t<O>(h, delta, sm, e);
+    fast_two_sum_t<O>(sm, O::add(l, e), nh, nl);
 }
 
 // Row fields (FP64 / FP32): 0..2 Q^n, 3..5 Q*, 6 pressure ratio -- the seven values
@@ -166,9 +193,9 @@ template <int PREC> struct EulerPolicy {
             const T c = (kind == 1) ? k.hlam : k.lam;
             T *out = row + (kind == 1 ? 3 : 0) * rs;
             const T q0 = row[s], q1 = row[rs + s], q2 = row[2 * rs + s];
-            out[s] = O::sub(q0, O::mul(c, O::sub(scr[s + 1], scr[s])));
-            out[rs + s] = O::sub(q1, O::mul(c, O::sub(scr[rs + s + 1], scr[rs + s])));
-            out[2 * rs + s] = O::sub(q2, O::mul(c, O::sub(scr[2 * rs + s + 1], scr[2 * rs + s])));
+            out[s] = eu_update<O>(q0, c, O::sub(scr[s + 1], scr[s]));
+            out[rs + s] = eu_update<O>(q1, c, O::sub(scr[rs + s + 1], scr[rs + s]));
+            out[2 * rs + s] = eu_update<O>(q2, c, O::sub(scr[2 * rs + s + 1], scr[2 * rs + s]));
         }
     }
 };
@@ -241,18 +268,13 @@ struct EulerPolicyComp {
                              __fsub_rn(scr[2 * rs + s + 1], scr[2 * rs + s])};
             if (kind == 1) {
 #pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    T h = row[v * rs + s], l = row[(3 + v) * rs + s];
-                    row[(6 + v) * rs + s] = __fadd_rn(h, __fsub_rn(l, __fmul_rn(k.hlam, df[v])));
-                }
+                for (int v = 0; v < 3; ++v)
+                    row[(6 + v) * rs + s] = eu_comp_predict<O>(row[v * rs + s], row[(3 + v) * rs + s], k.hlam, df[v]);
             } else {
 #pragma unroll
                 for (int v = 0; v < 3; ++v) {
-                    T h = row[v * rs + s], l = row[(3 + v) * rs + s];
-                    T delta = -__fmul_rn(k.lam, df[v]);
-                    T sm, e, nh, nl;
-                    two_sum(h, delta, sm, e);
-                    fast_two_sum(sm, __fadd_rn(l, e), nh, nl);
+                    T nh, nl;
+                    eu_comp_final<O>(row[v * rs + s], row[(3 + v) * rs + s], k.lam, df[v], nh, nl);
                     row[v * rs + s] = nh;
                     row[(3 + v) * rs + s] = nl;
                 }

@@ -4,12 +4,14 @@
 #pragma once
 #include <cstdint>
 
+#include "common.cuh"
+
 namespace sw {
 
 // Flank buffer element ((f * S + b) * 2 + side) * W + (2*j + k):
 // field f, structure b, side 0 = left / 1 = right, level offset j, cell k of the pair.
 template <class T>
-__device__ __forceinline__ int64_t flank_off(int64_t S, int W, int f, int64_t b, int side) {
+SW_HD int64_t flank_off(int64_t S, int W, int f, int64_t b, int side) {
     return ((f * S + b) * 2 + side) * (int64_t)W;
 }
 

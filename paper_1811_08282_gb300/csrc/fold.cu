@@ -27,6 +27,7 @@ static cudaError_t go(const FoldPhase &ph, const HeatParams &prm, int64_t warps,
     a.p = ph.p;
     a.n = ph.n;
     a.tiles = ph.M;
+    a.nstruct = ph.nstruct;
     a.nstruct_max = ph.S;
     a.lower = ph.lower;
     a.upper = ph.upper;
@@ -35,8 +36,7 @@ static cudaError_t go(const FoldPhase &ph, const HeatParams &prm, int64_t warps,
     a.flank_in = reinterpret_cast<const T *>(ph.flank_in);
     a.flank_out = reinterpret_cast<T *>(ph.flank_out);
     a.state = reinterpret_cast<T *>(ph.state);
-    const int64_t M = ph.M;
-    if (warps > M) warps = M;
+    if (warps > ph.nstruct) warps = ph.nstruct;
     if (warps < 1) warps = 1;
     const int64_t blocks = (warps + 3) / 4;  // 4 warps per CTA
     k_heat_fold<K, C><<<(unsigned)blocks, 128, 0, st>>>(a, prm);

@@ -21,6 +21,7 @@ bool fold_supported(int precision, int W);
 struct FoldPhase {
     int p;
     int64_t n, M, S;
+    int64_t nstruct;  // structures 0 .. nstruct-1 of the phase run here (M, or fewer in a hybrid run)
     int lower, upper, write_lower, write_upper;
     const void *flank_in;
     void *flank_out;

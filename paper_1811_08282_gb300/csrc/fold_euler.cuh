@@ -50,12 +50,12 @@ template <class O_> struct EFoldPlain {
     // predictor: Q* = Q^n - (lambda/2) dF
     static __device__ __forceinline__ void predict(T (&c)[NF], const EulerK<O> &k, const T (&d)[3]) {
 #pragma unroll
-        for (int v = 0; v < 3; ++v) c[QS + v] = O::sub(c[v], O::mul(k.hlam, d[v]));
+        for (int v = 0; v < 3; ++v) c[QS + v] = eu_update<O>(c[v], k.hlam, d[v]);
     }
     // final: Q^{n+1} = Q^n - lambda dF
     static __device__ __forceinline__ void final_(T (&c)[NF], const EulerK<O> &k, const T (&d)[3]) {
 #pragma unroll
-        for (int v = 0; v < 3; ++v) c[v] = O::sub(c[v], O::mul(k.lam, d[v]));
+        for (int v = 0; v < 3; ++v) c[v] = eu_update<O>(c[v], k.lam, d[v]);
     }
 };
 
@@ -68,18 +68,11 @@ struct EFoldComp {
     static constexpr int MIN_BLOCKS = 4;  // 16 warps per SM, the best of a sweep
     static __device__ __forceinline__ void predict(T (&c)[NF], const EulerK<O> &k, const T (&d)[3]) {
 #pragma unroll
-        for (int v = 0; v < 3; ++v) c[QS + v] = __fadd_rn(c[v], __fsub_rn(c[3 + v], __fmul_rn(k.hlam, d[v])));
+        for (int v = 0; v < 3; ++v) c[QS + v] = eu_comp_predict<O>(c[v], c[3 + v], k.hlam, d[v]);
     }
     static __device__ __forceinline__ void final_(T (&c)[NF], const EulerK<O> &k, const T (&d)[3]) {
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            const T delta = -__fmul_rn(k.lam, d[v]);
-            T sm, e, nh, nl;
-            two_sum(c[v], delta, sm, e);
-            fast_two_sum(sm, __fadd_rn(c[3 + v], e), nh, nl);
-            c[v] = nh;
-            c[3 + v] = nl;
-        }
+        for (int v = 0; v < 3; ++v) eu_comp_final<O>(c[v], c[3 + v], k.lam, d[v], c[v], c[3 + v]);
     }
 };
 

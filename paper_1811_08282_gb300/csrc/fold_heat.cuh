@@ -77,6 +77,7 @@ template <class T> struct FoldArgs {
     int p;                // 0: Up Triangle; 1: seam-centred phase (odd); 2: tile-centred (even)
     int64_t n;            // cells
     int64_t tiles;        // M (periodic: structures per phase)
+    int64_t nstruct;      // structures run by this launch: 0 .. nstruct-1 (M, or fewer in a hybrid run)
     int64_t nstruct_max;  // structures per flank buffer (flank layout of k_swept_phase)
     int lower, upper;     // levels of the lower / upper halves in this phase
     int write_lower;      // Down Triangle: the lower half ends at the run's last level; store its row
@@ -118,8 +119,8 @@ __global__ void __launch_bounds__(128) k_heat_fold(FoldArgs<typename C::T> a, He
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t M = a.tiles;
-    const int64_t b0 = gw * M / nw, b1 = (gw + 1) * M / nw;
+    const int64_t M = a.tiles, NS = a.nstruct;
+    const int64_t b0 = gw * NS / nw, b1 = (gw + 1) * NS / nw;
     if (b0 >= b1) return;  // whole warp
     const int64_t S = a.nstruct_max;
     const int64_t plane = S * 2 * (int64_t)W;  // flank field stride (FoldComp: low parts)

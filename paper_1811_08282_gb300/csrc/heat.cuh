@@ -11,9 +11,9 @@ namespace sw {
 // ============================================================================
 // Heat
 // ============================================================================
+#pragma nv_exec_check_disable
 template <class O>
-__device__ __forceinline__ typename O::T heat_update(typename O::T r, typename O::T a,
-                                                     typename O::T u, typename O::T b) {
+SW_HD typename O::T heat_update(typename O::T r, typename O::T a, typename O::T u, typename O::T b) {
     using T = typename O::T;
     return O::fma_(r, O::fma_(T(-2), u, O::add(a, b)), u);
 }
@@ -26,18 +26,25 @@ struct HL {
 // formed from exactly-split differences of the high parts plus the low parts,
 // scaled by r = rh + rl, and added to the state with TwoSum so that increments
 // far below half an ulp of u are kept in the low part instead of rounding away.
-__device__ __forceinline__ HL heat_update_comp(float rh, float rl, HL a, HL u, HL b) {
+// O: OpsF on the device, HostOpsF on the host.
+#pragma nv_exec_check_disable
+template <class O>
+SW_HD HL heat_update_comp_t(float rh, float rl, HL a, HL u, HL b) {
     float d1, e1, d2, e2;
-    two_sum(a.h, -u.h, d1, e1);
-    two_sum(b.h, -u.h, d2, e2);
-    float low = __fadd_rn(__fadd_rn(e1, e2), __fmaf_rn(-2.0f, u.l, __fadd_rn(a.l, b.l)));
-    float d = __fadd_rn(__fadd_rn(d1, d2), low);
-    float delta = __fmaf_rn(rh, d, __fmul_rn(rl, d));
+    two_sum_t<O>(a.h, -u.h, d1, e1);
+    two_sum_t<O>(b.h, -u.h, d2, e2);
+    const float low = O::add(O::add(e1, e2), O::fma_(-2.0f, u.l, O::add(a.l, b.l)));
+    const float d = O::add(O::add(d1, d2), low);
+    const float delta = O::fma_(rh, d, O::mul(rl, d));
     float s, e;
-    two_sum(u.h, delta, s, e);
+    two_sum_t<O>(u.h, delta, s, e);
     HL out;
-    fast_two_sum(s, __fadd_rn(u.l, e), out.h, out.l);
+    fast_two_sum_t<O>(s, O::add(u.l, e), out.h, out.l);
     return out;
+}
+
+__device__ __forceinline__ HL heat_update_comp(float rh, float rl, HL a, HL u, HL b) {
+    return heat_update_comp_t<OpsF>(rh, rl, a, u, b);
 }
 
 struct HeatParams {

@@ -171,23 +171,22 @@ __global__ void __launch_bounds__(256) k_euler_stage(typename O::T *__restrict__
         const T d0 = O::sub(fx[tid + 1], fx[tid]);
         const T d1 = O::sub(fx[(B + 1) + tid + 1], fx[(B + 1) + tid]);
         const T d2 = O::sub(fx[2 * (B + 1) + tid + 1], fx[2 * (B + 1) + tid]);
-        if (!COMP) {
+        if constexpr (!COMP) {
             const T c = FINAL ? k.lam : k.hlam;
             T *dst = FINAL ? q : s;
-            dst[i] = O::sub(q[i], O::mul(c, d0));
-            dst[n + i] = O::sub(q[n + i], O::mul(c, d1));
-            dst[2 * n + i] = O::sub(q[2 * n + i], O::mul(c, d2));
+            dst[i] = eu_update<O>(q[i], c, d0);
+            dst[n + i] = eu_update<O>(q[n + i], c, d1);
+            dst[2 * n + i] = eu_update<O>(q[2 * n + i], c, d2);
         } else {
             const T dv[3] = {d0, d1, d2};
 #pragma unroll
             for (int v = 0; v < 3; ++v) {
                 const float h = q[v * n + i], lo = q[(3 + v) * n + i];
                 if (!FINAL) {
-                    s[v * n + i] = __fadd_rn(h, __fsub_rn(lo, __fmul_rn(k.hlam, dv[v])));
+                    s[v * n + i] = eu_comp_predict<O>(h, lo, k.hlam, dv[v]);
                 } else {
-                    float sm, e, nh, nl;
-                    two_sum(h, -__fmul_rn(k.lam, dv[v]), sm, e);
-                    fast_two_sum(sm, __fadd_rn(lo, e), nh, nl);
+                    float nh, nl;
+                    eu_comp_final<O>(h, lo, k.lam, dv[v], nh, nl);
                     q[v * n + i] = nh;
                     q[(3 + v) * n + i] = nl;
                 }

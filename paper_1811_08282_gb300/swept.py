@@ -35,7 +35,7 @@ EXPORTS = (
     "sw_last_launch_count", "sw_tile_width", "sw_status_string", "sw_abi_version",
     "sw_set_timing", "sw_launch_times", "sw_run_noalloc",
     "sw_batch_create", "sw_batch_run", "sw_batch_status", "sw_batch_items", "sw_batch_debug",
-    "sw_batch_destroy", "sw_autotune",
+    "sw_batch_destroy", "sw_autotune", "sw_hybrid_split", "sw_run_hybrid",
 )
 
 
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH):
         "sw_state_bytes": ([P], i64),
         "sw_run": ([vp, vp, i64, vp], ctypes.c_int),
         "sw_run_host": ([vp, vp, vp, i64, vp], ctypes.c_int),
+        "sw_hybrid_split": ([i64, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
+        "sw_run_hybrid": ([vp, vp, i64, i32, i32, vp], ctypes.c_int),
         "sw_pack_fp64": ([P, vp, vp, vp], ctypes.c_int),
         "sw_unpack_fp64": ([P, vp, vp, vp], ctypes.c_int),
         "sw_conservation": ([vp, vp, ctypes.POINTER(dbl), vp], ctypes.c_int),
@@ -236,6 +238,11 @@ class Handle:
         _check(load().sw_run_host(self._h, _ptr(state_in), _ptr(state_out), int(nsteps), _stream(stream)),
                "sw_run_host")
 
+    def sw_run_hybrid(self, state, nsteps: int, work_factor: int, cpu_threads: int, stream=None) -> None:
+        """Swept run shared with `cpu_threads` host threads (GPU work factor `work_factor`)."""
+        _check(load().sw_run_hybrid(self._h, _ptr(state), int(nsteps), int(work_factor), int(cpu_threads),
+                                    _stream(stream)), "sw_run_hybrid")
+
     def sw_conservation(self, state, stream=None):
         sums = (ctypes.c_double * 3)()
         _check(load().sw_conservation(self._h, _ptr(state), sums, _stream(stream)), "sw_conservation")
@@ -267,6 +274,14 @@ class Handle:
         kind = (ctypes.c_int32 * cap)()
         cnt = _check(int(load().sw_launch_times(self._h, ms, kind, int(cap))), "sw_launch_times")
         return [(float(ms[i]), int(kind[i])) for i in range(cnt)]
+
+
+def sw_hybrid_split(tiles: int, work_factor: int, cpu_threads: int):
+    """(gpu_tiles, tiles_per_thread) of the affinity split (Eq. 1's work factor)."""
+    g, per = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().sw_hybrid_split(int(tiles), int(work_factor), int(cpu_threads), ctypes.byref(g), ctypes.byref(per)),
+           "sw_hybrid_split")
+    return g.value, per.value
 
 
 def sw_create(problem: Problem) -> Handle:
