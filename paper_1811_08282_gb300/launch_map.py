@@ -6,10 +6,15 @@ the best W per N and fits the Swept time per step to a power law y = A x^b
 (Table 1, least squares, with R^2). This module runs that experiment on this
 library: every (N, W) for the swept method, and the per-step ("Classic") kernel
 once per N (it has no tile width), each timed with CUDA events after one
-untimed run. There is no GPU work factor here: the whole domain is on the GPU.
+untimed run. With --work-factors the map gains the paper's third axis, the GPU
+work factor of Eq. 1: each (N, W) is also run split between the GPU and
+--threads host threads (sw_run_hybrid; 0 = the GPU alone), timed on the host
+clock around the synchronous call.
 
     python -m paper_1811_08282_gb300.launch_map --scheme heat --precision fp64
     python -m paper_1811_08282_gb300.launch_map --scheme euler --precision fp64 --exps 14 20
+    python -m paper_1811_08282_gb300.launch_map --scheme heat --exps 19 23 --step 2 \
+        --work-factors 0 32 64 96 --threads 16
 
 Output: one JSON line per measurement ({"kind": "point", ...}), one per N with
 the best W and the swept speedup over per-step ({"kind": "best", ...}), and one
@@ -66,9 +71,12 @@ def _initial(scheme, n):
     return I.sod(n)
 
 
-def measure(scheme: str, precision: int, n: int, method: int, W: int, steps: int, reps: int) -> float:
+def measure(scheme: str, precision: int, n: int, method: int, W: int, steps: int, reps: int,
+            work_factor: int = 0, threads: int = 0) -> float:
     """Seconds per run of `steps` time steps (minimum over `reps` timed runs after one
-    untimed run), state resident on the device, reset from a device copy each run."""
+    untimed run), state resident on the device, reset from a device copy each run;
+    work_factor > 0: the hybrid run with `threads` host threads."""
+    import time
     import torch
     p = _problem(scheme, precision, n, method, W)
     x0 = torch.as_tensor(_initial(scheme, n).reshape(-1), device="cuda")
@@ -78,6 +86,13 @@ def measure(scheme: str, precision: int, n: int, method: int, W: int, steps: int
     with S.Handle(p) as h:
         for i in range(reps + 1):
             st.copy_(fresh)
+            if work_factor > 0:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                h.sw_run_hybrid(st, steps, work_factor, threads)
+                if i:
+                    ts.append(time.perf_counter() - t0)
+                continue
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record()
@@ -93,7 +108,7 @@ def measure(scheme: str, precision: int, n: int, method: int, W: int, steps: int
 
 
 def run_map(scheme: str, precision: int, exps, widths, target: float, cap: int, reps: int, emit=print,
-            fit_exps=None):
+            fit_exps=None, work_factors=(0,), threads: int = 1):
     """Measure every (N, W) and per-step per N; fit the best swept time per step over
     N in 2^fit_exps[0] .. 2^fit_exps[1] (default: every measured N)."""
     best = []
@@ -103,20 +118,27 @@ def run_map(scheme: str, precision: int, exps, widths, target: float, cap: int, 
         steps = steps_for(scheme, n, target, max(ws), cap)
         row = {}
         for W in ws:
-            t = measure(scheme, precision, n, S.SW_SWEPT, W, steps, reps)
-            row[W] = t
-            emit(json.dumps({"kind": "point", "scheme": scheme, "precision": precision, "n": n, "method": "swept",
-                             "W": W, "steps": steps, "us_per_step": t / steps * 1e6,
-                             "gcell_steps_per_s": n * steps / t / 1e9}))
+            for wf in work_factors:
+                if wf > 0:
+                    try:
+                        S.sw_hybrid_split(n // W, wf, threads)
+                    except S.SweptError:
+                        continue  # too few tiles for this split
+                t = measure(scheme, precision, n, S.SW_SWEPT, W, steps, reps, wf, threads)
+                row[(W, wf)] = t
+                emit(json.dumps({"kind": "point", "scheme": scheme, "precision": precision, "n": n,
+                                 "method": "swept" if wf == 0 else "hybrid", "W": W, "work_factor": wf,
+                                 "threads": threads if wf else 0, "steps": steps, "us_per_step": t / steps * 1e6,
+                                 "gcell_steps_per_s": n * steps / t / 1e9}))
         tc = measure(scheme, precision, n, S.SW_PERSTEP, 0, steps, reps)
         emit(json.dumps({"kind": "point", "scheme": scheme, "precision": precision, "n": n, "method": "perstep",
                          "W": None, "steps": steps, "us_per_step": tc / steps * 1e6,
                          "gcell_steps_per_s": n * steps / tc / 1e9}))
         wb = min(row, key=row.get)
         best.append((n, row[wb] / steps * 1e6))
-        emit(json.dumps({"kind": "best", "scheme": scheme, "precision": precision, "n": n, "W": wb,
-                         "swept_us_per_step": row[wb] / steps * 1e6, "perstep_us_per_step": tc / steps * 1e6,
-                         "speedup": tc / row[wb]}))
+        emit(json.dumps({"kind": "best", "scheme": scheme, "precision": precision, "n": n, "W": wb[0],
+                         "work_factor": wb[1], "swept_us_per_step": row[wb] / steps * 1e6,
+                         "perstep_us_per_step": tc / steps * 1e6, "speedup": tc / row[wb]}))
     lo, hi = fit_exps if fit_exps else (0, 62)
     pts = [(n, y) for n, y in best if (1 << lo) <= n <= (1 << hi)]
     A, b, r2 = power_fit([n for n, _ in pts], [y for _, y in pts])
@@ -137,14 +159,19 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--fit-exps", type=int, nargs=2, default=None,
                     help="log2 N range of the power-law fit (default: all measured)")
+    ap.add_argument("--work-factors", type=int, nargs="+", default=[0],
+                    help="GPU work factors (Eq. 1) to map; 0 = the GPU alone")
+    ap.add_argument("--threads", type=int, default=None, help="host threads of the hybrid runs (default: all cores)")
     a = ap.parse_args(argv)
     import torch
     from . import build
     build.build()
     torch.cuda.set_device(0)
     target = a.target if a.target is not None else (2.0 ** 32 if a.scheme == "heat" else 2.0 ** 28)
+    import os
+    threads = a.threads or (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
     run_map(a.scheme, PREC[a.precision], range(a.exps[0], a.exps[1] + 1, a.step), a.widths, target, a.cap, a.reps,
-            fit_exps=a.fit_exps)
+            fit_exps=a.fit_exps, work_factors=a.work_factors, threads=threads)
 
 
 if __name__ == "__main__":
