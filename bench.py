@@ -342,12 +342,17 @@ def run_ours(args):
     small = {}
     n_s, steps_s = 16384, 1000
     u_s = torch.as_tensor(I_mod().heat_initial(I_mod().heat_modes(n_s, 8, seed=0)), device=dev)
-    for key, prec, method, W in (("fp64_swept_w64", S.SW_FP64, S.SW_SWEPT, 64),
-                                 ("fp64_perstep", S.SW_FP64, S.SW_PERSTEP, 0),
-                                 ("fp32_swept_w128", S.SW_FP32, S.SW_SWEPT, 128),
-                                 ("fp32_perstep", S.SW_FP32, S.SW_PERSTEP, 0)):
+    # "_graph": the run captured once into a CUDA graph and replayed (SW_FLAG_GRAPH)
+    for key, prec, method, W, flags in (("fp64_swept_w64", S.SW_FP64, S.SW_SWEPT, 64, 0),
+                                        ("fp64_perstep", S.SW_FP64, S.SW_PERSTEP, 0, 0),
+                                        ("fp32_swept_w128", S.SW_FP32, S.SW_SWEPT, 128, 0),
+                                        ("fp32_perstep", S.SW_FP32, S.SW_PERSTEP, 0, 0),
+                                        ("fp64_swept_w64_graph", S.SW_FP64, S.SW_SWEPT, 64, S.SW_FLAG_GRAPH),
+                                        ("fp64_perstep_graph", S.SW_FP64, S.SW_PERSTEP, 0, S.SW_FLAG_GRAPH),
+                                        ("fp32_swept_w128_graph", S.SW_FP32, S.SW_SWEPT, 128, S.SW_FLAG_GRAPH),
+                                        ("fp32_perstep_graph", S.SW_FP32, S.SW_PERSTEP, 0, S.SW_FLAG_GRAPH)):
         ps = S.Problem(scheme=S.SW_HEAT, precision=prec, boundary=S.SW_PERIODIC, method=method, n=n_s,
-                       r=0.25, tile_width=W)
+                       r=0.25, tile_width=W, flags=flags)
         st = S.to_state(ps, u_s)
         fresh = st.clone()
         with S.Handle(ps) as hs:
@@ -356,6 +361,8 @@ def run_ours(args):
             small[key] = {"ms": t * 1e3, "value": n_s * steps_s / t / 1e9, "launches": hs.sw_last_launch_count()}
     small["speedup_fp64"] = small["fp64_perstep"]["ms"] / small["fp64_swept_w64"]["ms"]
     small["speedup_fp32"] = small["fp32_perstep"]["ms"] / small["fp32_swept_w128"]["ms"]
+    small["speedup_fp64_graphs"] = small["fp64_perstep_graph"]["ms"] / small["fp64_swept_w64_graph"]["ms"]
+    small["speedup_fp32_graphs"] = small["fp32_perstep_graph"]["ms"] / small["fp32_swept_w128_graph"]["ms"]
     compare["small_grid_n16384_1000_steps"] = small
 
     # batched: 4096 independent problems (half heat, half Euler, lengths 2^10..2^18), FP32 hi/lo,

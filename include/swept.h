@@ -90,6 +90,19 @@ extern "C" {
                                 arithmetic and the folded kernel evaluates K + 1 faces per K
                                 cells per level at a lower occupancy. Ignored with
                                 SW_FLAG_GENERIC. */
+/* The two data-structure strategies of Section 4.3 (Fig. 2) for the Euler step; every
+   form gives the same bits. By default swept runs are lengthened (four 3-point
+   sub-steps per step, the pressure ratio stored between them) and per-step runs are
+   flattened (two 5-point stages per step, two launches). */
+#define SW_FLAG_LENGTHENED 4 /* per-step Euler: the lengthened form, four launches per step */
+#define SW_FLAG_GRAPH 16     /* sw_run captures the run's launches once into a CUDA graph
+                                (on a private stream, launch tracing off) and replays it on the
+                                caller's stream; the handle keeps one graph, for the last
+                                (state pointer, nsteps) pair, and captures again when either
+                                changes. Same results. */
+#define SW_FLAG_FLATTENED 8  /* swept Euler: the flattened form, two 5-point stages per step
+                                (windows widen and narrow by 2 cells per level, W/4 levels per
+                                phase); generic kernel only (ignores SW_FLAG_EULER_FOLD) */
 
 #define SW_MIN_TILE 4
 #define SW_MAX_TILE 1024
@@ -107,7 +120,7 @@ typedef struct sw_problem {
     double gamma;       /* Euler: ratio of specific heats (> 1) */
     int32_t tile_width; /* swept base width W: even, SW_MIN_TILE..SW_MAX_TILE,
                            divides n; 0 selects the library default */
-    int32_t flags;      /* 0 or SW_FLAG_GENERIC | SW_FLAG_EULER_FOLD (sw_run_noalloc: must be 0) */
+    int32_t flags;      /* 0 or an OR of the SW_FLAG_* bits above (sw_run_noalloc, batches: must be 0) */
 } sw_problem;
 
 typedef struct sw_handle sw_handle;

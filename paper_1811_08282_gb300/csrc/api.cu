@@ -115,6 +115,11 @@ struct sw_handle {
     void *h_state = nullptr;
     HostPool *pool = nullptr;
     cudaEvent_t hy_ev[2] = {nullptr, nullptr};
+    // SW_FLAG_GRAPH: the captured run for the last (state, nsteps) pair
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    void *g_state = nullptr;
+    int64_t g_steps = -1, g_launches = 0;
 };
 
 namespace {
@@ -131,13 +136,16 @@ int planes_of(const sw_problem &p) {
 
 size_t elem_size(const sw_problem &p) { return p.precision == SW_FP64 ? sizeof(double) : sizeof(float); }
 
+bool flattened(const sw_problem &p) { return p.scheme == SW_EULER && (p.flags & SW_FLAG_FLATTENED); }
+
 int validate(const sw_problem *p) {
     if (!p) return SW_ERR_BAD_ARG;
     if (p->scheme != SW_HEAT && p->scheme != SW_EULER) return SW_ERR_BAD_ARG;
     if (p->precision < SW_FP64 || p->precision > SW_FP32_COMP) return SW_ERR_BAD_ARG;
     if (p->boundary != SW_PERIODIC && p->boundary != SW_TRANSMISSIVE) return SW_ERR_BAD_ARG;
     if (p->method != SW_SWEPT && p->method != SW_PERSTEP) return SW_ERR_BAD_ARG;
-    if (p->flags & ~(SW_FLAG_GENERIC | SW_FLAG_EULER_FOLD)) return SW_ERR_BAD_ARG;
+    if (p->flags & ~(SW_FLAG_GENERIC | SW_FLAG_EULER_FOLD | SW_FLAG_LENGTHENED | SW_FLAG_FLATTENED | SW_FLAG_GRAPH))
+        return SW_ERR_BAD_ARG;
     if (p->n < 4 || p->n > (int64_t(1) << 40)) return SW_ERR_BAD_ARG;
     if (p->scheme == SW_HEAT) {
         if (!(p->r > 0.0) || !(p->r < 1e6)) return SW_ERR_BAD_ARG;
@@ -149,6 +157,8 @@ int validate(const sw_problem *p) {
         if (W != 0) {
             if (W < SW_MIN_TILE || W > SW_MAX_TILE || (W & 1)) return SW_ERR_BAD_ARG;
             if (p->n % W != 0 || p->n < 2 * (int64_t)W) return SW_ERR_BAD_ARG;
+            // flattened Euler: radius-2 windows, W/4 levels per phase half
+            if (flattened(*p) && (W % 4 != 0 || W < 8)) return SW_ERR_BAD_ARG;
         }
     } else if (p->tile_width != 0 && (p->tile_width < 0)) {
         return SW_ERR_BAD_ARG;
@@ -159,7 +169,7 @@ int validate(const sw_problem *p) {
 // Default base width: the largest of 1024, 512, ..., 4 that divides n with at
 // least two tiles (Section 6 recommends large blocks, 768-1024).
 int default_width(const sw_problem &p) {
-    for (int W = SW_MAX_TILE; W >= SW_MIN_TILE; W >>= 1)
+    for (int W = SW_MAX_TILE; W >= (flattened(p) ? 8 : SW_MIN_TILE); W >>= 1)
         if (p.n % W == 0 && p.n >= 2 * (int64_t)W) return W;
     return 0;
 }
@@ -201,8 +211,11 @@ inline void trace_end(sw_handle *h, int64_t i, cudaStream_t st) {
     }
 }
 
-// Host scheme matching each GPU storage policy (same fields, same per-cell arithmetic).
-template <class P> struct HostOf;
+// Host scheme matching each GPU storage policy (same fields, same per-cell arithmetic);
+// void for policies the host share does not run (the flattened form).
+template <class P> struct HostOf {
+    using type = void;
+};
 template <> struct HostOf<HeatPolicy<0>> {
     using type = HostHeatPlain<HostOpsD>;
     static type make(const sw_handle *h) { return type{h->hp.r}; }
@@ -261,7 +274,8 @@ template <class P>
 int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st, Hybrid *hy = nullptr) {
     using T = typename P::T;
     const int H = h->H, W = h->W;
-    const int64_t P_last = (L + H - 1) / H;
+    const int HL = H / P::R;  // levels per phase half
+    const int64_t P_last = (L + HL - 1) / HL;
     const bool periodic = h->prob.boundary == SW_PERIODIC;
     // periodic heat at W = 32K: every phase except a truncated upper half (which stores its
     // row mid-way) runs on the register-resident kernel
@@ -269,16 +283,19 @@ int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st, Hybrid *
                       !(h->prob.flags & SW_FLAG_GENERIC) && fold_supported(h->prob.precision, W);
     const int64_t fold_warps = int64_t(h->sms) * fold_warps_per_sm(h->prob.precision, W);
     // Euler at W = 128 (and 256 in FP32), on request only (it is the slower kernel on GB300)
-    const bool efold = std::is_same<typename P::Params, EulerParams>::value &&
+    const bool efold = std::is_same<typename P::Params, EulerParams>::value && P::R == 1 &&
                        (h->prob.flags & SW_FLAG_EULER_FOLD) && !(h->prob.flags & SW_FLAG_GENERIC) &&
                        euler_fold_supported(h->prob.precision, W);
     const int64_t efold_warps = int64_t(h->sms) * euler_fold_warps_per_sm(h->prob.precision, W);
     int64_t launches = 0;
     using Sch = typename HostOf<P>::type;
-    std::vector<Sch> sch;
+    constexpr bool kHost = !std::is_void<Sch>::value;
+    using SchV = typename std::conditional<kHost, Sch, int>::type;
+    std::vector<SchV> sch;
     std::vector<std::vector<T>> work;
     std::vector<WrittenRange> written;
-    if (hy) {
+    if (hy && !kHost) return SW_ERR_BAD_ARG;
+    if constexpr (kHost) if (hy) {
         const int nt = h->pool->size();
         for (int t = 0; t < nt; ++t) sch.push_back(HostOf<P>::make(h));
         work.assign(nt, std::vector<T>(size_t(2) * Sch::NF * (W + 2)));
@@ -296,11 +313,11 @@ int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st, Hybrid *
         a.periodic = periodic ? 1 : 0;
         // the kernel needs only "Up or not" and the parity of p
         a.p = (p == 0) ? 0 : (int)(2 - (p & 1));
-        a.F = p * H;
-        a.lower = (p == 0) ? 0 : (int)std::min<int64_t>(H, L - (p - 1) * H);
-        a.upper = (p == P_last) ? 0 : (int)std::min<int64_t>(H - 1, L - p * H);
+        a.F = p * HL;
+        a.lower = (p == 0) ? 0 : (int)std::min<int64_t>(HL, L - (p - 1) * HL);
+        a.upper = (p == P_last) ? 0 : (int)std::min<int64_t>(HL - 1, L - p * HL);
         a.write_lower = (p == P_last) ? 1 : 0;
-        a.write_upper = (a.upper > 0 && p * H + a.upper == L) ? 1 : 0;
+        a.write_upper = (a.upper > 0 && p * HL + a.upper == L) ? 1 : 0;
         a.tiles = h->M;
         a.nstruct = (p & 1) ? (periodic ? h->M : h->M + 1) : h->M;
         a.nstruct_max = h->S;
@@ -337,7 +354,7 @@ int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st, Hybrid *
         }
         trace_end(h, launches, st);
         ++launches;
-        if (hy) {
+        if constexpr (kHost) if (hy) {
             // the GPU's flank slot of phase p that a host structure of phase p+1 reads: the
             // last GPU tile Mg-1 (p even), or the seam structure 0 across the periodic wrap (p odd)
             const int64_t slot = (p == P_last) ? -1 : ((p & 1) == 0 ? hy->Mg - 1 : (periodic ? 0 : -1));
@@ -360,7 +377,7 @@ int launch_swept(sw_handle *h, void *state, int64_t L, cudaStream_t st, Hybrid *
         }
     }
     h->last_launches = launches;
-    if (hy) {
+    if constexpr (kHost) if (hy) {
         for (const WrittenRange &w : written) {
             hy->first = std::min(hy->first, w.first);
             hy->last = std::max(hy->last, w.last);
@@ -436,6 +453,26 @@ int launch_perstep_euler_t(sw_handle *h, void *state, int64_t nsteps, cudaStream
     const unsigned grid = (unsigned)((n + B - 1) / B);
     T *q = reinterpret_cast<T *>(state);
     T *s = reinterpret_cast<T *>(h->scratch);
+    if (h->prob.flags & SW_FLAG_LENGTHENED) {
+        // lengthened form: four 3-point sub-step launches per step
+        const size_t smem4 = (size_t(4) * (B + 2) + size_t(3) * (B + 1)) * sizeof(T);
+        for (int64_t k = 0; k < nsteps; ++k) {
+            trace_begin(h, 4 * k, 3, st);
+            k_euler_sub<O, 0, COMP><<<grid, B, smem4, st>>>(q, s, n, h->ep, periodic);
+            trace_end(h, 4 * k, st);
+            trace_begin(h, 4 * k + 1, 3, st);
+            k_euler_sub<O, 1, COMP><<<grid, B, smem4, st>>>(q, s, n, h->ep, periodic);
+            trace_end(h, 4 * k + 1, st);
+            trace_begin(h, 4 * k + 2, 3, st);
+            k_euler_sub<O, 2, COMP><<<grid, B, smem4, st>>>(q, s, n, h->ep, periodic);
+            trace_end(h, 4 * k + 2, st);
+            trace_begin(h, 4 * k + 3, 3, st);
+            k_euler_sub<O, 3, COMP><<<grid, B, smem4, st>>>(q, s, n, h->ep, periodic);
+            trace_end(h, 4 * k + 3, st);
+        }
+        h->last_launches = 4 * nsteps;
+        return cuda_status(cudaGetLastError());
+    }
     for (int64_t k = 0; k < nsteps; ++k) {
         trace_begin(h, 2 * k, 3, st);
         k_euler_stage<O, false, COMP><<<grid, B, smem, st>>>(q, s, n, h->ep, periodic);
@@ -616,6 +653,15 @@ int sw_create(const sw_problem *p, sw_handle **out) {
             default: h->nsnap = HeatPolicy<2>::NSNAP; h->smem = swept_smem<HeatPolicy<2>>(h->W);
                 prc = prepare_swept_kernel<HeatPolicy<2>>(h->smem); break;
             }
+        } else if (flattened(*p)) {
+            switch (p->precision) {
+            case SW_FP64: h->nsnap = EulerFlatPolicy<0>::NSNAP; h->smem = swept_smem<EulerFlatPolicy<0>>(h->W);
+                prc = prepare_swept_kernel<EulerFlatPolicy<0>>(h->smem); break;
+            case SW_FP32: h->nsnap = EulerFlatPolicy<1>::NSNAP; h->smem = swept_smem<EulerFlatPolicy<1>>(h->W);
+                prc = prepare_swept_kernel<EulerFlatPolicy<1>>(h->smem); break;
+            default: h->nsnap = EulerFlatPolicyComp::NSNAP; h->smem = swept_smem<EulerFlatPolicyComp>(h->W);
+                prc = prepare_swept_kernel<EulerFlatPolicyComp>(h->smem); break;
+            }
         } else {
             switch (p->precision) {
             case SW_FP64: h->nsnap = EulerPolicy<0>::NSNAP; h->smem = swept_smem<EulerPolicy<0>>(h->W);
@@ -635,7 +681,7 @@ int sw_create(const sw_problem *p, sw_handle **out) {
         }
     } else {
         if (p->scheme == SW_HEAT) h->scratch_bytes = size_t(h->nio) * p->n * h->esize;
-        else h->scratch_bytes = size_t(3) * p->n * h->esize;  // Q* planes
+        else h->scratch_bytes = size_t(4) * p->n * h->esize;  // Q* planes, ratio plane (lengthened form)
         e = cudaMalloc(&h->scratch, h->scratch_bytes);
         if (e != cudaSuccess) return fail(cuda_status(e));
     }
@@ -668,6 +714,8 @@ void sw_destroy(sw_handle *h) {
     cudaFreeHost(h->h_state);
     for (cudaEvent_t e : h->hy_ev)
         if (e) cudaEventDestroy(e);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
     delete h->pool;
     delete h;
 }
@@ -703,12 +751,10 @@ int64_t sw_launch_times(sw_handle *h, float *ms, int32_t *kind, int64_t cap) {
     return cnt;
 }
 
-int sw_run(sw_handle *h, void *state, int64_t nsteps, void *stream) {
-    if (!h || !state || nsteps < 0) return SW_ERR_BAD_ARG;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    h->last_launches = 0;
-    h->ev_used = 0;
-    if (nsteps == 0) return SW_OK;
+namespace {
+
+// The launches of one run (swept phases or per-step launches), enqueued on `st`.
+int run_direct(sw_handle *h, void *state, int64_t nsteps, cudaStream_t st) {
     const sw_problem &p = h->prob;
     if (p.method == SW_SWEPT) {
         const int64_t L = nsteps * (p.scheme == SW_HEAT ? 1 : 4);
@@ -717,6 +763,14 @@ int sw_run(sw_handle *h, void *state, int64_t nsteps, void *stream) {
             case SW_FP64: return launch_swept<HeatPolicy<0>>(h, state, L, st);
             case SW_FP32: return launch_swept<HeatPolicy<1>>(h, state, L, st);
             default: return launch_swept<HeatPolicy<2>>(h, state, L, st);
+            }
+        }
+        if (flattened(p)) {
+            const int64_t L2 = 2 * nsteps;  // two stages per step
+            switch (p.precision) {
+            case SW_FP64: return launch_swept<EulerFlatPolicy<0>>(h, state, L2, st);
+            case SW_FP32: return launch_swept<EulerFlatPolicy<1>>(h, state, L2, st);
+            default: return launch_swept<EulerFlatPolicyComp>(h, state, L2, st);
             }
         }
         switch (p.precision) {
@@ -731,6 +785,59 @@ int sw_run(sw_handle *h, void *state, int64_t nsteps, void *stream) {
     case SW_FP32: return launch_perstep_euler_t<OpsF, false>(h, state, nsteps, st);
     default: return launch_perstep_euler_t<OpsF, true>(h, state, nsteps, st);
     }
+}
+
+// SW_FLAG_GRAPH: capture the run once on a private stream (tracing off), keep the
+// instantiated graph for this (state, nsteps) pair, replay it on the caller's stream.
+int run_graph(sw_handle *h, void *state, int64_t nsteps, cudaStream_t st) {
+    if (!(h->gexec && h->g_state == state && h->g_steps == nsteps)) {
+        cudaError_t e = cudaSuccess;
+        if (!h->gstream) e = cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (h->gexec) {
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+        const int64_t cap = h->ev_cap;
+        h->ev_cap = 0;
+        e = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            h->ev_cap = cap;
+            return cuda_status(e);
+        }
+        const int rc = run_direct(h, state, nsteps, h->gstream);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(h->gstream, &g);
+        h->ev_cap = cap;
+        if (rc != SW_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return rc != SW_OK ? rc : cuda_status(e);
+        }
+        e = cudaGraphInstantiate(&h->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->gexec = nullptr;
+            return cuda_status(e);
+        }
+        h->g_state = state;
+        h->g_steps = nsteps;
+        h->g_launches = h->last_launches;
+    }
+    h->last_launches = h->g_launches;
+    h->ev_used = 0;
+    return cuda_status(cudaGraphLaunch(h->gexec, st));
+}
+
+}  // namespace
+
+int sw_run(sw_handle *h, void *state, int64_t nsteps, void *stream) {
+    if (!h || !state || nsteps < 0) return SW_ERR_BAD_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    h->last_launches = 0;
+    h->ev_used = 0;
+    if (nsteps == 0) return SW_OK;
+    if (h->prob.flags & SW_FLAG_GRAPH) return run_graph(h, state, nsteps, st);
+    return run_direct(h, state, nsteps, st);
 }
 
 int sw_hybrid_split(int64_t tiles, int32_t work_factor, int32_t cpu_threads, int64_t *gpu_tiles,
@@ -748,7 +855,7 @@ int sw_hybrid_split(int64_t tiles, int32_t work_factor, int32_t cpu_threads, int
 int sw_run_hybrid(sw_handle *h, void *state, int64_t nsteps, int32_t work_factor, int32_t cpu_threads,
                   void *stream) {
     if (!h || !state || nsteps < 0) return SW_ERR_BAD_ARG;
-    if (h->prob.method != SW_SWEPT) return SW_ERR_BAD_ARG;
+    if (h->prob.method != SW_SWEPT || flattened(h->prob)) return SW_ERR_BAD_ARG;
     int64_t Mg = 0;
     int rc = sw_hybrid_split(h->M, work_factor, cpu_threads, &Mg, nullptr);
     if (rc != SW_OK) return rc;

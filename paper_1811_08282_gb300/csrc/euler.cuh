@@ -127,6 +127,7 @@ template <int PREC> struct EulerPolicy {
     using T = typename O::T;
     static constexpr int NROW = 7, NSNAP = 7, NIO = 3;
     static constexpr bool INJECT_AHEAD = false;
+    static constexpr int R = 1;  // stencil radius: windows change by R cells per level
     static constexpr bool TWO_PASS = true;
     static constexpr int NSCR = 3;  // face flux components (or the pressure) per position
     // launch bound: FP32 keeps 64 registers (4 CTAs of 256 threads per SM), FP64 up to 128
@@ -208,6 +209,7 @@ struct EulerPolicyComp {
     using T = float;
     static constexpr int NROW = 10, NSNAP = 10, NIO = 6;
     static constexpr bool INJECT_AHEAD = false;
+    static constexpr int R = 1;  // stencil radius: windows change by R cells per level
     static constexpr bool TWO_PASS = true;
     static constexpr int NSCR = 3;
     static constexpr int MIN_BLOCKS = 2;
@@ -283,4 +285,91 @@ struct EulerPolicyComp {
     }
 };
 
+// Flattened form (Section 4.3, Fig. 2): two 5-point stages per step, one level
+// each (level % 2: 0 predictor from Q, 1 final from Q*); the pressure ratio is
+// recomputed inside the stage instead of being stored. Stencil radius 2: a swept
+// window changes by two cells per level and a flank entry pair becomes a quad.
+// Row fields: Q^n (0..2), Q* (3..5); hi/lo: Q^n high (0..2), low (3..5), Q* (6..8).
+// Four passes per level over the window [lo, hi]: pressures on [lo-2, hi+2],
+// ratios on [lo-1, hi+1], face fluxes between s-1 and s for s in [lo, hi+1], the
+// update on [lo, hi]. Every value is the one the lengthened form computes.
+// Scratch fields: pressure (0), ratio (1), face flux (2..4).
+template <class O_, bool COMP> struct EulerFlatBase {
+    using O = O_;
+    using T = typename O::T;
+    static constexpr int NROW = COMP ? 9 : 6, NSNAP = NROW, NIO = COMP ? 6 : 3;
+    static constexpr int QS = COMP ? 6 : 3;
+    static constexpr int R = 2;
+    static constexpr int NSCR = 5;
+    static constexpr bool INJECT_AHEAD = false;
+    static constexpr bool TWO_PASS = false;
+    static constexpr int MIN_BLOCKS = std::is_same<T, float>::value ? 2 : 1;
+    using Params = EulerParams;
+    static __device__ __forceinline__ void load_state(T *row, int rs, int s, const T *st, int64_t n, int64_t j) {
+#pragma unroll
+        for (int f = 0; f < NIO; ++f) row[f * rs + s] = st[f * n + j];
+    }
+    static __device__ __forceinline__ void store_state(const T *row, int rs, int s, int64_t level, T *st,
+                                                       int64_t n, int64_t j) {
+#pragma unroll
+        for (int f = 0; f < NIO; ++f) st[f * n + j] = row[f * rs + s];
+    }
+    static __device__ __forceinline__ T get_field(const T *row, int rs, int s, int64_t level, int f) {
+        return row[f * rs + s];
+    }
+    static __device__ __forceinline__ void set_field(T *row, int rs, int s, int64_t level, int f, T v) {
+        row[f * rs + s] = v;
+    }
+    static __device__ __forceinline__ const T *group(const T *row, int rs, int64_t level) {
+        return row + ((level & 1) == 0 ? 0 : QS) * rs;
+    }
+    static __device__ __forceinline__ void pass_p(const Params &prm, const T *row, int rs, T *scr, int s,
+                                                  int64_t level) {
+        const EulerK<O> k = eu_k<O>(prm);
+        const T *q = group(row, rs, level);
+        scr[s] = eu_pressure<O>(k, q[s], q[rs + s], q[2 * rs + s]);
+    }
+    static __device__ __forceinline__ void pass_th(T *scr, int rs, int s) {
+        scr[rs + s] = eu_ratio<O>(scr[s - 1], scr[s], scr[s + 1]);
+    }
+    static __device__ __forceinline__ void pass_f(const Params &prm, const T *row, int rs, T *scr, int s,
+                                                  int64_t level) {
+        const EulerK<O> k = eu_k<O>(prm);
+        const T *q = group(row, rs, level);
+        const T *th = scr + rs;
+        T f0, f1, f2;
+        eu_face_flux<O>(k, q[s - 1], q[rs + s - 1], q[2 * rs + s - 1], th[s - 1], q[s], q[rs + s], q[2 * rs + s],
+                        th[s], f0, f1, f2);
+        scr[2 * rs + s] = f0;
+        scr[3 * rs + s] = f1;
+        scr[4 * rs + s] = f2;
+    }
+    static __device__ __forceinline__ void pass_u(const Params &prm, T *row, int rs, const T *scr, int s,
+                                                  int64_t level) {
+        const EulerK<O> k = eu_k<O>(prm);
+        const bool pred = (level & 1) == 0;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const T d = O::sub(scr[(2 + v) * rs + s + 1], scr[(2 + v) * rs + s]);
+            if constexpr (!COMP) {
+                if (pred) row[(QS + v) * rs + s] = eu_update<O>(row[v * rs + s], k.hlam, d);
+                else row[v * rs + s] = eu_update<O>(row[v * rs + s], k.lam, d);
+            } else {
+                if (pred) {
+                    row[(QS + v) * rs + s] = eu_comp_predict<O>(row[v * rs + s], row[(3 + v) * rs + s], k.hlam, d);
+                } else {
+                    float nh, nl;
+                    eu_comp_final<O>(row[v * rs + s], row[(3 + v) * rs + s], k.lam, d, nh, nl);
+                    row[v * rs + s] = nh;
+                    row[(3 + v) * rs + s] = nl;
+                }
+            }
+        }
+    }
+};
+
+template <int PREC> using EulerFlatPolicy = EulerFlatBase<typename std::conditional<PREC == 0, OpsD, OpsF>::type, false>;
+using EulerFlatPolicyComp = EulerFlatBase<OpsF, true>;
+
 }  // namespace sw
+

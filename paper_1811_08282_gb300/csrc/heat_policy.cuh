@@ -15,6 +15,7 @@ template <> struct HeatPolicy<0> {  // FP64
     using O = OpsD;
     static constexpr int NROW = 2, NSNAP = 1, NIO = 1;
     static constexpr bool INJECT_AHEAD = true;
+    static constexpr int R = 1;  // stencil radius: windows change by R cells per level
     static constexpr bool TWO_PASS = false;
     static constexpr int NSCR = 0;
     static constexpr int MIN_BLOCKS = 4;  // launch bound: resident 512-thread blocks per SM
@@ -48,6 +49,7 @@ template <> struct HeatPolicy<1> {  // FP32
     using O = OpsF;
     static constexpr int NROW = 2, NSNAP = 1, NIO = 1;
     static constexpr bool INJECT_AHEAD = true;
+    static constexpr int R = 1;  // stencil radius: windows change by R cells per level
     static constexpr bool TWO_PASS = false;
     static constexpr int NSCR = 0;
     static constexpr int MIN_BLOCKS = 4;  // launch bound: resident 512-thread blocks per SM
@@ -80,6 +82,7 @@ template <> struct HeatPolicy<2> {  // FP32 hi/lo compensated
     using T = float;
     static constexpr int NROW = 4, NSNAP = 2, NIO = 2;  // row: h0 l0 h1 l1; planes: hi, lo
     static constexpr bool INJECT_AHEAD = true;
+    static constexpr int R = 1;  // stencil radius: windows change by R cells per level
     static constexpr bool TWO_PASS = false;
     static constexpr int NSCR = 0;
     static constexpr int MIN_BLOCKS = 3;  // launch bound: resident 512-thread blocks per SM

@@ -195,4 +195,69 @@ __global__ void __launch_bounds__(256) k_euler_stage(typename O::T *__restrict__
     }
 }
 
+// One sub-step of the lengthened Euler step (Section 4.3, Fig. 2: four 3-point
+// sub-steps per step, the pressure ratio stored between them), one launch each:
+// KIND 0 ratio of Q, 1 predictor Q*, 2 ratio of Q*, 3 final. q: the state planes
+// (COMP: high 3, low 3); s: scratch planes Q* (0..2) and ratio (3). A block of B
+// cells stages its cells plus one halo cell per side; transmissive ends clamp the
+// halo to the end cell, whose ratio is 0 (its one-sided difference vanishes), so the
+// halo is the scheme's ghost cell. Same per-cell functions as every other form.
+template <class O, int KIND, bool COMP>
+__global__ void __launch_bounds__(256) k_euler_sub(typename O::T *__restrict__ q, typename O::T *__restrict__ s,
+                                                   int64_t n, EulerParams prm, int periodic) {
+    using T = typename O::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int B = blockDim.x, NL = B + 2;
+    T *g = reinterpret_cast<T *>(smem_raw);  // [3][NL] flux / pressure group, cells x0-1 .. x0+B
+    T *aux = g + 3 * NL;                      // [NL] pressure (ratio kinds) or ratio (flux kinds)
+    T *fx = aux + NL;                         // [3][B+1] face fluxes x0-1/2 .. x0+B-1/2
+    const EulerK<O> k = eu_k<O>(prm);
+    const int tid = threadIdx.x;
+    const int64_t x0 = (int64_t)blockIdx.x * B;
+    const T *src = (KIND <= 1) ? q : s;  // Q (high parts) or Q*
+    for (int l = tid; l < NL; l += B) {
+        const int64_t j = nb_index(x0 - 1 + l, n, periodic);
+        const T r0 = src[j], r1 = src[n + j], r2 = src[2 * n + j];
+        g[l] = r0;
+        g[NL + l] = r1;
+        g[2 * NL + l] = r2;
+        if constexpr (KIND == 0 || KIND == 2) aux[l] = eu_pressure<O>(k, r0, r1, r2);
+        else aux[l] = s[3 * n + j];
+    }
+    __syncthreads();
+    const int64_t i = x0 + tid;
+    if constexpr (KIND == 0 || KIND == 2) {
+        if (i < n) s[3 * n + i] = eu_ratio<O>(aux[tid], aux[tid + 1], aux[tid + 2]);
+    } else {
+        for (int m = tid; m <= B; m += B) {
+            T f0, f1, f2;
+            eu_face_flux<O>(k, g[m], g[NL + m], g[2 * NL + m], aux[m], g[m + 1], g[NL + m + 1], g[2 * NL + m + 1],
+                            aux[m + 1], f0, f1, f2);
+            fx[m] = f0;
+            fx[(B + 1) + m] = f1;
+            fx[2 * (B + 1) + m] = f2;
+        }
+        __syncthreads();
+        if (i < n) {
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                const T d = O::sub(fx[v * (B + 1) + tid + 1], fx[v * (B + 1) + tid]);
+                if constexpr (!COMP) {
+                    if constexpr (KIND == 1) s[v * n + i] = eu_update<O>(q[v * n + i], k.hlam, d);
+                    else q[v * n + i] = eu_update<O>(q[v * n + i], k.lam, d);
+                } else {
+                    if constexpr (KIND == 1) {
+                        s[v * n + i] = eu_comp_predict<O>(q[v * n + i], q[(3 + v) * n + i], k.hlam, d);
+                    } else {
+                        float nh, nl;
+                        eu_comp_final<O>(q[v * n + i], q[(3 + v) * n + i], k.lam, d, nh, nl);
+                        q[v * n + i] = nh;
+                        q[(3 + v) * n + i] = nl;
+                    }
+                }
+            }
+        }
+    }
+}
+
 }  // namespace sw

@@ -55,21 +55,33 @@ template <bool CG, class T> __device__ __forceinline__ T flank_ld(const T *p) {
 constexpr int kFlankChunk = 32;
 
 // Shared memory of one structure, in elements of P::T: the row (NROW fields of
-// W+2 positions), for two-pass policies per-position scratch (NSCR fields of
-// W+2), and a chunk of staged input flank entries. Output flank entries go from
-// the row to global memory directly.
+// W+2R positions), per-position scratch (NSCR fields), and a chunk of staged input
+// flank entries (2R per level and side). Output flank entries go from the row to
+// global memory directly.
 template <class P> __host__ __device__ constexpr size_t swept_smem_elems(int W) {
-    return size_t(P::NROW) * (W + 2) + size_t(P::NSCR) * (W + 2) + size_t(P::NSNAP) * 4 * (kFlankChunk + 1);
+    return size_t(P::NROW + P::NSCR) * (W + 2 * P::R) + size_t(P::NSNAP) * 2 * 2 * P::R * (kFlankChunk + 1);
 }
 
-// One sub-step over row positions [lo, hi]: two-pass policies first compute
-// per-position intermediates on [lo-1, hi+1] into scratch, then update cells.
+// One sub-step over row positions [lo, hi]. Radius 1: two-pass policies first
+// compute per-position intermediates on [lo-1, hi+1] into scratch, then update
+// cells. Radius 2 (flattened Euler stage): pressures, ratios, faces, update.
 template <class P, class GL, class GR, class AFTER>
 __device__ __forceinline__ void swept_level(const typename P::Params &prm, typename P::T *row, int rs,
                                             typename P::T *scr, int64_t lev, int lo, int hi, int slo, int shi,
                                             GL ghost_l, GR ghost_r, AFTER after) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    if constexpr (P::TWO_PASS) {
+    if constexpr (P::R == 2) {
+        for (int s = lo - 2 + tid; s <= hi + 2; s += nt) P::pass_p(prm, row, rs, scr, s, lev);
+        __syncthreads();
+        for (int s = lo - 1 + tid; s <= hi + 1; s += nt) P::pass_th(scr, rs, s);
+        __syncthreads();
+        for (int s = lo + tid; s <= hi + 1; s += nt) P::pass_f(prm, row, rs, scr, s, lev);
+        __syncthreads();
+        for (int s = lo + tid; s <= hi; s += nt) {
+            P::pass_u(prm, row, rs, scr, s, lev);
+            after(s);
+        }
+    } else if constexpr (P::TWO_PASS) {
         for (int s = lo - 1 + tid; s <= hi + 1; s += nt)
             P::pre(prm, row, rs, scr, s, lev, lo, hi, slo, shi, ghost_l(s), ghost_r(s - 1));
         __syncthreads();
@@ -87,31 +99,51 @@ __device__ __forceinline__ void swept_level(const typename P::Params &prm, typen
 
 // The work of one structure (triangle or diamond) `b` of one phase, done by one
 // CTA (all its threads must call it). smem: swept_smem_elems<P>(W) elements.
+// Stencil radius R = P::R: a phase half spans HL = H / R levels, the lower half's
+// window [c - R i, c + R i) widens and the upper half's [c - H + R i, c + H - R i)
+// narrows by R cells per side and level, and a flank entry per level and side is
+// the 2R outermost cells (2R HL = W entries per side, the layout of R = 1).
 template <class P, bool CG>
 __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &a,
                                                 const typename P::Params &prm, int64_t b,
                                                 typename P::T *smem) {
     using T = typename P::T;
+    constexpr int R = P::R, R2 = 2 * P::R;
     T *row = smem;
-    const int W = a.W, H = a.H;
-    const int rs = W + 2;                 // row stride (positions 0..W+1)
-    T *scr = row + P::NROW * rs;          // [NSCR][W+2] (two-pass policies)
-    T *chunk = scr + P::NSCR * rs;        // [NSNAP][2 sides][2 (kFlankChunk + 1)] staged flank entries
+    const int W = a.W, H = a.H, HL = a.H / R;
+    const int rs = W + 2 * R;             // row stride (positions 0..W+2R-1)
+    T *scr = row + P::NROW * rs;          // [NSCR][rs]
+    T *chunk = scr + P::NSCR * rs;        // [NSNAP][2 sides][2R (kFlankChunk + 1)] staged flank entries
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t n = a.n;
     const int64_t S = a.nstruct_max;
     const int64_t c = (a.p & 1) ? b * W : b * W + H;
-    const int64_t base = c - H - 1;       // cell of row position 0
+    const int64_t base = c - H - R;       // cell of row position 0
 
     // valid row positions (transmissive domains clip to [0, n))
-    int slo = 0, shi = W + 1;
+    int slo = 0, shi = rs - 1;
     if (!a.periodic) {
         if (base < 0) slo = (int)(-base);
-        if (base + W + 1 > n - 1) shi = (int)(n - 1 - base);
+        if (base + rs - 1 > n - 1) shi = (int)(n - 1 - base);
     }
     auto cell = [&](int s) -> int64_t { return a.periodic ? wrap_index(base + s, n) : base + s; };
     auto ghost_l = [&](int s) -> bool { return !a.periodic && base + s == 0; };
     auto ghost_r = [&](int s) -> bool { return !a.periodic && base + s == n - 1; };
+    // radius 2: the cells beyond a transmissive end are copies of the end cell (the
+    // clamped halo of the per-step flattened kernel); refreshed before every level
+    auto ghost_fill = [&](int64_t lev) {
+        if constexpr (R == 2) {
+            if (slo == 0 && shi == rs - 1) return;
+            for (int t = tid; t < 2 * R * P::NROW; t += nt) {
+                const int side = t / (R * P::NROW), rem = t % (R * P::NROW), d = rem / P::NROW + 1,
+                          f = rem % P::NROW;
+                const int s = side == 0 ? slo - d : shi + d, src = side == 0 ? slo : shi;
+                if ((side == 0 ? slo > 0 : shi < rs - 1) && s >= 0 && s < rs)
+                    P::set_field(row, rs, s, lev, f, P::get_field(row, rs, src, lev, f));
+            }
+            __syncthreads();
+        }
+    };
     // this structure's flank entry e of `side` (0 left, 1 right) at level `lev`: every field
     auto publish = [&](int s, int64_t lev, int side, int e) {
         if (!a.flank_out || a.upper <= 0) return;
@@ -119,15 +151,17 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
         for (int f = 0; f < P::NSNAP; ++f)
             a.flank_out[flank_off<T>(S, W, f, b, side) + e] = P::get_field(row, rs, s, lev, f);
     };
+    // the full row (level F): flank entries j = 0, the 2R outermost cells of each side
+    auto publish_full = [&](int s, int64_t lev) {
+        if (s >= R && s < R + R2) publish(s, lev, 0, s - R);
+        if (s >= W - R && s < W + R) publish(s, lev, 1, s - (W - R));
+    };
 
     if (a.p == 0) {
         // Up Triangle: the initial row [c-H, c+H) at level 0 (always inside the domain)
-        for (int s = 1 + tid; s <= W; s += nt) {
+        for (int s = R + tid; s < W + R; s += nt) {
             P::load_state(row, rs, s, a.state, n, base + s);
-            if (s == 1) publish(s, 0, 0, 0);      // flank entries of level 0 (j = 0)
-            if (s == 2) publish(s, 0, 0, 1);
-            if (s == W - 1) publish(s, 0, 1, 0);
-            if (s == W) publish(s, 0, 1, 1);
+            publish_full(s, 0);
         }
         __syncthreads();
     } else {
@@ -144,28 +178,28 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
             if (a.p & 1) { has_l = b > 0; has_r = b < a.tiles; }
         }
         // Communication: the neighbours' flank entries are staged in chunks of CH levels
-        // (all fields, both sides, one overlapping entry pair so that an injection one
+        // (all fields, both sides, one overlapping entry group so that an injection one
         // level ahead stays inside the chunk), loaded cooperatively from global memory;
-        // step i injects the flank pair of level F-H+i-1 from the chunk into the row.
-        const int cs = 2 * (kFlankChunk + 1);  // entries per (field, side) in the chunk
-        int i0 = 1;                            // first step the chunk serves
+        // step i injects the flank group of level F-HL+i-1 from the chunk into the row.
+        const int cs = R2 * (kFlankChunk + 1);  // entries per (field, side) in the chunk
+        int i0 = 1;                             // first step the chunk serves
         auto load_chunk = [&](int first) {
             i0 = first;
             for (int t = tid; t < P::NSNAP * 2 * cs; t += nt) {
                 const int f = t / (2 * cs), rem = t % (2 * cs), side = rem / cs, e = rem % cs;
-                const int64_t idx = 2 * (int64_t)(first - 1) + e;
+                const int64_t idx = (int64_t)R2 * (first - 1) + e;
                 if (idx < W && (side == 0 ? has_l : has_r))
                     chunk[t] = flank_ld<CG>(a.flank_in +
                                             flank_off<T>(S, W, f, side == 0 ? lb : rb, side == 0 ? 1 : 0) + idx);
             }
         };
         auto inject = [&](int i) {
-            for (int t = tid; t < 4 * P::NSNAP; t += nt) {
-                const int side = t / (2 * P::NSNAP), rem = t % (2 * P::NSNAP);
+            for (int t = tid; t < 2 * R2 * P::NSNAP; t += nt) {
+                const int side = t / (R2 * P::NSNAP), rem = t % (R2 * P::NSNAP);
                 const int k = rem / P::NSNAP, f = rem % P::NSNAP;
-                const int s = side == 0 ? H - i + k : H + i + k;
+                const int s = side == 0 ? H - R * i + k : H + R * i + k;
                 if ((side == 0 ? has_l : has_r) && s >= slo && s <= shi)
-                    P::set_field(row, rs, s, a.F - H + i - 1, f, chunk[(f * 2 + side) * cs + 2 * (i - i0) + k]);
+                    P::set_field(row, rs, s, a.F - HL + i - 1, f, chunk[(f * 2 + side) * cs + R2 * (i - i0) + k]);
             }
         };
         if (a.lower > 0) {
@@ -177,7 +211,7 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
             __syncthreads();
         }
         for (int i = 1; i <= a.lower; ++i) {
-            const int64_t lev = a.F - H + i - 1;  // level read; level lev+1 written
+            const int64_t lev = a.F - HL + i - 1;  // level read; level lev+1 written
             if (i > 1 && (i - 1) % kFlankChunk == 0) {  // the previous level ended with a barrier
                 load_chunk(i);
                 __syncthreads();
@@ -186,17 +220,13 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
                 inject(i);
                 __syncthreads();
             }
-            int lo = H + 1 - i, hi = H + i;
+            ghost_fill(lev);
+            int lo = H + R - R * i, hi = H + R + R * i - 1;
             if (lo < slo) lo = slo;
             if (hi > shi) hi = shi;
             const bool last = (i == a.lower);
             swept_level<P>(prm, row, rs, scr, lev, lo, hi, slo, shi, ghost_l, ghost_r, [&](int s) {
-                if (i == H) {  // full level F reached: flank entries j = 0
-                    if (s == 1) publish(s, lev + 1, 0, 0);
-                    if (s == 2) publish(s, lev + 1, 0, 1);
-                    if (s == W - 1) publish(s, lev + 1, 1, 0);
-                    if (s == W) publish(s, lev + 1, 1, 1);
-                }
+                if (i == HL) publish_full(s, lev + 1);  // full level F reached
                 if (last && a.write_lower) P::store_state(row, rs, s, lev + 1, a.state, n, cell(s));
             });
             if (P::INJECT_AHEAD && i < a.lower) inject(i + 1);
@@ -207,15 +237,15 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
     // upper half: levels F+1 .. F+upper on the narrowing window; flank entries j = i
     for (int i = 1; i <= a.upper; ++i) {
         const int64_t lev = a.F + i - 1;
-        int lo = 1 + i, hi = W - i;
+        ghost_fill(lev);
+        int lo = R + R * i, hi = W + R - 1 - R * i;
+        const int el = lo, er = hi + 1 - R2;  // first position of the left / right entry group
         if (lo < slo) lo = slo;
         if (hi > shi) hi = shi;
         const bool last = (i == a.upper);
         swept_level<P>(prm, row, rs, scr, lev, lo, hi, slo, shi, ghost_l, ghost_r, [&](int s) {
-            if (s == 1 + i) publish(s, lev + 1, 0, 2 * i);
-            if (s == 2 + i) publish(s, lev + 1, 0, 2 * i + 1);
-            if (s == W - 1 - i) publish(s, lev + 1, 1, 2 * i);
-            if (s == W - i) publish(s, lev + 1, 1, 2 * i + 1);
+            if (s >= el && s < el + R2) publish(s, lev + 1, 0, R2 * i + (s - el));
+            if (s >= er && s < er + R2) publish(s, lev + 1, 1, R2 * i + (s - er));
             if (last && a.write_upper) P::store_state(row, rs, s, lev + 1, a.state, n, cell(s));
         });
         __syncthreads();

@@ -15,6 +15,11 @@ clock around the synchronous call.
     python -m paper_1811_08282_gb300.launch_map --scheme euler --precision fp64 --exps 14 20
     python -m paper_1811_08282_gb300.launch_map --scheme heat --exps 19 23 --step 2 \
         --work-factors 0 32 64 96 --threads 16
+    python -m paper_1811_08282_gb300.launch_map --scheme euler --forms --exps 14 22
+
+--forms (Euler) is Section 4.3's experiment (Fig. 3): the time per step of the two
+data-structure strategies, lengthened (four 3-point sub-steps per step) and
+flattened (two 5-point stages), each with the swept rule (best W) and per step.
 
 Output: one JSON line per measurement ({"kind": "point", ...}), one per N with
 the best W and the swept speedup over per-step ({"kind": "best", ...}), and one
@@ -57,12 +62,12 @@ def steps_for(scheme: str, n: int, target: float, wmax: int, cap: int) -> int:
     return int(min(max(lo, target // n), max(lo, cap)))
 
 
-def _problem(scheme, precision, n, method, W):
+def _problem(scheme, precision, n, method, W, flags=0):
     if scheme == "heat":
         return S.Problem(scheme=S.SW_HEAT, precision=precision, boundary=S.SW_PERIODIC, method=method,
-                         n=n, r=0.3, tile_width=W)
+                         n=n, r=0.3, tile_width=W, flags=flags)
     return S.Problem(scheme=S.SW_EULER, precision=precision, boundary=S.SW_TRANSMISSIVE, method=method,
-                     n=n, dt_dx=I.sod_lambda(), gamma=I.GAMMA, tile_width=W)
+                     n=n, dt_dx=I.sod_lambda(), gamma=I.GAMMA, tile_width=W, flags=flags)
 
 
 def _initial(scheme, n):
@@ -72,13 +77,13 @@ def _initial(scheme, n):
 
 
 def measure(scheme: str, precision: int, n: int, method: int, W: int, steps: int, reps: int,
-            work_factor: int = 0, threads: int = 0) -> float:
+            work_factor: int = 0, threads: int = 0, flags: int = 0) -> float:
     """Seconds per run of `steps` time steps (minimum over `reps` timed runs after one
     untimed run), state resident on the device, reset from a device copy each run;
     work_factor > 0: the hybrid run with `threads` host threads."""
     import time
     import torch
-    p = _problem(scheme, precision, n, method, W)
+    p = _problem(scheme, precision, n, method, W, flags)
     x0 = torch.as_tensor(_initial(scheme, n).reshape(-1), device="cuda")
     fresh = S.to_state(p, x0)
     st = fresh.clone()
@@ -147,6 +152,26 @@ def run_map(scheme: str, precision: int, exps, widths, target: float, cap: int, 
     return best, (A, b, r2)
 
 
+def run_forms(precision: int, exps, widths, target: float, cap: int, reps: int, emit=print):
+    """Section 4.3 / Fig. 3 on this GPU: µs per step of the four Euler forms per N."""
+    forms = {"swept_lengthened": (S.SW_SWEPT, 0), "swept_flattened": (S.SW_SWEPT, S.SW_FLAG_FLATTENED),
+             "perstep_flattened": (S.SW_PERSTEP, 0), "perstep_lengthened": (S.SW_PERSTEP, S.SW_FLAG_LENGTHENED)}
+    for e in exps:
+        n = 1 << e
+        ws = [W for W in widths if n % W == 0 and n >= 2 * W and W % 4 == 0 and W >= 8]
+        steps = steps_for("euler", n, target, max(ws), cap)
+        row = {}
+        for name, (method, flags) in forms.items():
+            if method == S.SW_SWEPT:
+                ts = {W: measure("euler", precision, n, method, W, steps, reps, flags=flags) for W in ws}
+                W = min(ts, key=ts.get)
+                row[name] = (ts[W] / steps * 1e6, W)
+            else:
+                row[name] = (measure("euler", precision, n, method, 0, steps, reps, flags=flags) / steps * 1e6, None)
+        emit(json.dumps({"kind": "forms", "precision": precision, "n": n, "steps": steps,
+                         **{k: {"us_per_step": v[0], "W": v[1]} for k, v in row.items()}}))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--scheme", choices=("heat", "euler"), default="heat")
@@ -162,12 +187,18 @@ def main(argv=None):
     ap.add_argument("--work-factors", type=int, nargs="+", default=[0],
                     help="GPU work factors (Eq. 1) to map; 0 = the GPU alone")
     ap.add_argument("--threads", type=int, default=None, help="host threads of the hybrid runs (default: all cores)")
+    ap.add_argument("--forms", action="store_true",
+                    help="Euler: time the lengthened and flattened forms, swept and per step (Section 4.3)")
     a = ap.parse_args(argv)
     import torch
     from . import build
     build.build()
     torch.cuda.set_device(0)
     target = a.target if a.target is not None else (2.0 ** 32 if a.scheme == "heat" else 2.0 ** 28)
+    if a.forms:
+        run_forms(PREC[a.precision], range(a.exps[0], a.exps[1] + 1, a.step), a.widths,
+                  a.target if a.target is not None else 2.0 ** 28, a.cap, a.reps)
+        return
     import os
     threads = a.threads or (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
     run_map(a.scheme, PREC[a.precision], range(a.exps[0], a.exps[1] + 1, a.step), a.widths, target, a.cap, a.reps,

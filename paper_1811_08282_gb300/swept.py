@@ -27,6 +27,9 @@ SW_NOALLOC_SCRATCH_BYTES = 16 << 20
 SW_MIN_TILE, SW_MAX_TILE = 4, 1024
 SW_FLAG_GENERIC = 1
 SW_FLAG_EULER_FOLD = 2
+SW_FLAG_LENGTHENED = 4
+SW_FLAG_FLATTENED = 8
+SW_FLAG_GRAPH = 16
 
 # every symbol declared in include/swept.h
 EXPORTS = (

@@ -66,10 +66,12 @@ def test_state_layout(lib, scheme, prec, planes, esize):
     dict(n=4096, precision=3),
     dict(n=4096, boundary=2),
     dict(n=4096, method=5),
-    dict(n=4096, flags=4),                   # unknown flag bit
+    dict(n=4096, flags=32),                  # unknown flag bit
     dict(n=2),
     dict(n=4096, scheme=S.SW_EULER, dt_dx=0.0),
     dict(n=4096, scheme=S.SW_EULER, dt_dx=0.1, gamma=1.0),
+    dict(n=600, scheme=S.SW_EULER, dt_dx=0.1, tile_width=6, flags=S.SW_FLAG_FLATTENED),   # flattened: W % 4
+    dict(n=64, scheme=S.SW_EULER, dt_dx=0.1, tile_width=4, flags=S.SW_FLAG_FLATTENED),    # flattened: W >= 8
 ])
 def test_bad_problems_are_rejected_before_any_device_work(lib, bad):
     kw = dict(n=4096, r=0.3, tile_width=64)
