@@ -592,7 +592,7 @@ def run_configs(args):
             rates[W] = t
         return min(rates, key=rates.get)
 
-    def compare(name, make, x0, steps, tune_steps, extra):
+    def compare(name, make, x0, steps, tune_steps, extra, flat=False):
         res = {"config": name, "n": x0.shape[-1], "steps": steps, **extra, "forms": {}}
         ref = None
         for pn, pv in precs.items():
@@ -602,6 +602,11 @@ def run_configs(args):
             form = {"W": W, "swept": x0.shape[-1] * steps / ts / 1e9, "perstep": x0.shape[-1] * steps / tp / 1e9,
                     "speedup": tp / ts, "launches_swept": ls, "launches_perstep": lp,
                     "swept_equals_perstep": bool(np.array_equal(xs, xp))}
+            if flat:  # Euler: the swept run in the flattened form of Section 4.3 (same bits)
+                Wf = best_width(lambda W: make(pv, S.SW_SWEPT, W, S.SW_FLAG_FLATTENED), x0, tune_steps)
+                tf, xf, _ = timed(make(pv, S.SW_SWEPT, Wf, S.SW_FLAG_FLATTENED), x0, steps)
+                form.update({"W_flattened": Wf, "swept_flattened": x0.shape[-1] * steps / tf / 1e9,
+                             "flattened_equals_lengthened": bool(np.array_equal(xf, xs))})
             if pn == "fp64":
                 ref = xs
             else:
@@ -631,12 +636,12 @@ def run_configs(args):
 
     # Euler Sod, N = 2^20, 20,000 steps, transmissive
     def euler(lam):
-        return lambda pv, m, W: S.Problem(scheme=S.SW_EULER, precision=pv, boundary=S.SW_TRANSMISSIVE, method=m,
-                                          n=1 << 20 if lam == "sod" else 1 << 22,
-                                          dt_dx=I.sod_lambda() if lam == "sod" else I.riemann_lambda(),
-                                          gamma=I.GAMMA, tile_width=W)
+        return lambda pv, m, W, flags=0: S.Problem(
+            scheme=S.SW_EULER, precision=pv, boundary=S.SW_TRANSMISSIVE, method=m,
+            n=1 << 20 if lam == "sod" else 1 << 22, dt_dx=I.sod_lambda() if lam == "sod" else I.riemann_lambda(),
+            gamma=I.GAMMA, tile_width=W, flags=flags)
     compare("Euler Sod N=2^20, 20000 steps, transmissive", euler("sod"), I.sod(1 << 20), 20_000, 512,
-            {"dt_dx": I.sod_lambda()})
+            {"dt_dx": I.sod_lambda()}, flat=True)
 
     # precision config: heat N = 2^22, r = 0.4, 100,000 steps; Euler N = 2^22, 64 random Riemann segments
     n = 1 << 22
@@ -645,7 +650,7 @@ def run_configs(args):
     compare("heat N=2^22 r=0.4, 100000 steps, 32 modes", heat, I.heat_initial(I.heat_modes(n, 32, seed=1))[None],
             100_000, 4096, {"r": 0.4})
     compare("Euler N=2^22, 64 random Riemann segments, 20000 steps, transmissive", euler("riemann"),
-            I.riemann_initial(I.riemann_segments(n, 64, 1)), 20_000, 512, {"dt_dx": I.riemann_lambda()})
+            I.riemann_initial(I.riemann_segments(n, 64, 1)), 20_000, 512, {"dt_dx": I.riemann_lambda()}, flat=True)
 
     # batched: 4096 problems, FP32 hi/lo, tuned widths, 10,000 steps in one persistent launch
     items = batched.default_items(4096, seed=7)
