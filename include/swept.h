@@ -120,7 +120,8 @@ typedef struct sw_problem {
     double gamma;       /* Euler: ratio of specific heats (> 1) */
     int32_t tile_width; /* swept base width W: even, SW_MIN_TILE..SW_MAX_TILE,
                            divides n; 0 selects the library default */
-    int32_t flags;      /* 0 or an OR of the SW_FLAG_* bits above (sw_run_noalloc, batches: must be 0) */
+    int32_t flags;      /* 0 or an OR of the SW_FLAG_* bits above (sw_run_noalloc: must be 0;
+                           batches: 0 or SW_FLAG_FLATTENED) */
 } sw_problem;
 
 typedef struct sw_handle sw_handle;
@@ -240,7 +241,8 @@ SW_API int sw_run_noalloc(const sw_problem *p, void *state, int64_t nsteps, void
  * (Section 6 of the paper tunes the block size per problem; the batched launch
  * and its device-side work queue are this library's addition.)
  * sw_batch_create: `count` problems (all of one precision, method SW_SWEPT,
- * flags 0, each with an explicit tile_width), problem i's device state at
+ * flags 0 or, for an Euler problem, SW_FLAG_FLATTENED (then W % 4 == 0 and
+ * W >= 8), each with an explicit tile_width), problem i's device state at
  * states[i] (layout as for sw_run, owned by the caller and used by every run),
  * each advanced `nsteps` time steps per sw_batch_run. Allocates the flank
  * buffers, per-structure completion flags and the work tables (owned by the

@@ -30,7 +30,7 @@ constexpr int kBatchThreads = 128;
 constexpr int kChunk = 8;  // structures per work item
 
 struct BatchDesc {
-    int32_t scheme, periodic, W, pad;
+    int32_t scheme, periodic, W, flat;  // flat: Euler in the flattened form (Section 4.3)
     int64_t n, M, S, L, P_last;
     int64_t chunks_even, chunks_odd;  // work items per even / odd phase
     int64_t ep_tile, ep_seam;         // offsets of this problem's flags in the flag array
@@ -58,21 +58,24 @@ struct BatchTables {
 
 template <int PREC> struct EulerPolicyOf { using type = EulerPolicy<PREC>; };
 template <> struct EulerPolicyOf<2> { using type = EulerPolicyComp; };
+template <int PREC> struct EulerFlatOf { using type = EulerFlatPolicy<PREC>; };
+template <> struct EulerFlatOf<2> { using type = EulerFlatPolicyComp; };
 
 template <class T>
 __device__ __forceinline__ PhaseArgs<T> batch_args(const BatchDesc &d, int64_t p) {
     PhaseArgs<T> a{};
     const int H = d.W / 2;
+    const int HL = d.flat ? H / 2 : H;  // levels per phase half (radius-2 windows when flattened)
     a.n = d.n;
     a.W = d.W;
     a.H = H;
     a.periodic = d.periodic;
     a.p = (p == 0) ? 0 : (int)(2 - (p & 1));
-    a.F = p * H;
-    a.lower = (p == 0) ? 0 : (int)min((int64_t)H, d.L - (p - 1) * H);
-    a.upper = (p == d.P_last) ? 0 : (int)min((int64_t)(H - 1), d.L - p * H);
+    a.F = p * HL;
+    a.lower = (p == 0) ? 0 : (int)min((int64_t)HL, d.L - (p - 1) * HL);
+    a.upper = (p == d.P_last) ? 0 : (int)min((int64_t)(HL - 1), d.L - p * HL);
     a.write_lower = (p == d.P_last) ? 1 : 0;
-    a.write_upper = (a.upper > 0 && p * H + a.upper == d.L) ? 1 : 0;
+    a.write_upper = (a.upper > 0 && p * HL + a.upper == d.L) ? 1 : 0;
     a.tiles = d.M;
     a.nstruct = (p & 1) ? (d.periodic ? d.M : d.M + 1) : d.M;
     a.nstruct_max = d.S;
@@ -96,6 +99,7 @@ template <int PREC>
 __global__ void __launch_bounds__(kBatchThreads, PREC == 0 ? 4 : 8) k_batch(BatchTables t) {
     using HP = HeatPolicy<PREC>;
     using EP = typename EulerPolicyOf<PREC>::type;
+    using EF = typename EulerFlatOf<PREC>::type;
     using T = typename HP::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
@@ -180,6 +184,9 @@ __global__ void __launch_bounds__(kBatchThreads, PREC == 0 ? 4 : 8) k_batch(Batc
             if (d.scheme == SW_HEAT) {
                 const PhaseArgs<T> a = batch_args<T>(d, p);
                 swept_structure<HP, true>(a, d.hp, b, smem);
+            } else if (d.flat) {
+                const PhaseArgs<T> a = batch_args<T>(d, p);
+                swept_structure<EF, true>(a, d.ep, b, smem);
             } else {
                 const PhaseArgs<T> a = batch_args<T>(d, p);
                 swept_structure<EP, true>(a, d.ep, b, smem);
@@ -201,7 +208,12 @@ int cuda_status_b(cudaError_t e) {
     return SW_ERR_CUDA;
 }
 
-size_t smem_for(int scheme, int prec, int W) {
+size_t smem_for(int scheme, int prec, int W, bool flat) {
+    if (flat) {
+        if (prec == SW_FP64) return swept_smem_elems<EulerFlatPolicy<0>>(W) * 8;
+        if (prec == SW_FP32) return swept_smem_elems<EulerFlatPolicy<1>>(W) * 4;
+        return swept_smem_elems<EulerFlatPolicyComp>(W) * 4;
+    }
     if (scheme == SW_HEAT) {
         if (prec == SW_FP64) return swept_smem_elems<HeatPolicy<0>>(W) * 8;
         if (prec == SW_FP32) return swept_smem_elems<HeatPolicy<1>>(W) * 4;
@@ -212,7 +224,8 @@ size_t smem_for(int scheme, int prec, int W) {
     return swept_smem_elems<EulerPolicyComp>(W) * 4;
 }
 
-int nsnap_for(int scheme, int prec) {
+int nsnap_for(int scheme, int prec, bool flat) {
+    if (flat) return prec == SW_FP32_COMP ? EulerFlatPolicyComp::NSNAP : EulerFlatPolicy<1>::NSNAP;
     if (scheme == SW_HEAT) return prec == SW_FP32_COMP ? 2 : 1;
     return prec == SW_FP32_COMP ? EulerPolicyComp::NSNAP : 7;
 }
@@ -260,7 +273,11 @@ int sw_batch_create(const sw_problem *probs, void *const *states, int32_t count,
     const int prec = probs[0].precision;
     for (int32_t i = 0; i < count; ++i) {
         const sw_problem &p = probs[i];
-        if (!states[i] || p.precision != prec || p.method != SW_SWEPT || p.flags != 0) return SW_ERR_BAD_ARG;
+        if (!states[i] || p.precision != prec || p.method != SW_SWEPT) return SW_ERR_BAD_ARG;
+        // flags: 0, or the flattened form for an Euler problem (radius-2 windows: W % 4 == 0, W >= 8)
+        const bool flat = p.flags == SW_FLAG_FLATTENED && p.scheme == SW_EULER;
+        if (p.flags != 0 && !flat) return SW_ERR_BAD_ARG;
+        if (flat && (p.tile_width % 4 != 0 || p.tile_width < 8)) return SW_ERR_BAD_ARG;
         if (p.scheme != SW_HEAT && p.scheme != SW_EULER) return SW_ERR_BAD_ARG;
         if (p.boundary != SW_PERIODIC && p.boundary != SW_TRANSMISSIVE) return SW_ERR_BAD_ARG;
         if (prec < SW_FP64 || prec > SW_FP32_COMP) return SW_ERR_BAD_ARG;
@@ -289,12 +306,13 @@ int sw_batch_create(const sw_problem *probs, void *const *states, int32_t count,
         d.scheme = p.scheme;
         d.periodic = p.boundary == SW_PERIODIC;
         d.W = p.tile_width;
+        d.flat = (p.scheme == SW_EULER && p.flags == SW_FLAG_FLATTENED) ? 1 : 0;
         d.n = p.n;
         d.M = p.n / p.tile_width;
         d.S = d.M + 1;
-        d.L = nsteps * (p.scheme == SW_HEAT ? 1 : 4);
-        const int64_t H = d.W / 2;
-        d.P_last = (d.L + H - 1) / H;
+        d.L = nsteps * (p.scheme == SW_HEAT ? 1 : (d.flat ? 2 : 4));
+        const int64_t HL = d.flat ? d.W / 4 : d.W / 2;  // levels per phase half
+        d.P_last = (d.L + HL - 1) / HL;
         d.chunks_even = (d.M + kChunk - 1) / kChunk;
         d.chunks_odd = ((d.periodic ? d.M : d.M + 1) + kChunk - 1) / kChunk;
         d.ep_tile = flag_total;
@@ -313,7 +331,7 @@ int sw_batch_create(const sw_problem *probs, void *const *states, int32_t count,
         d.ep.hlamf = (float)(0.5 * p.dt_dx);
         d.state = states[i];
         if (d.L > 0) {
-            const size_t fb = size_t(nsnap_for(p.scheme, prec)) * d.S * 2 * d.W * es;
+            const size_t fb = size_t(nsnap_for(p.scheme, prec, d.flat)) * d.S * 2 * d.W * es;
             for (int k = 0; k < 2; ++k) {
                 void *f = nullptr;
                 e = cudaMalloc(&f, fb);
@@ -323,7 +341,7 @@ int sw_batch_create(const sw_problem *probs, void *const *states, int32_t count,
             }
         }
         pmax = std::max(pmax, d.L > 0 ? d.P_last : (int64_t)-1);
-        b->smem = std::max(b->smem, smem_for(p.scheme, prec, d.W));
+        b->smem = std::max(b->smem, smem_for(p.scheme, prec, d.W, d.flat));
     }
     if (b->smem > 227 * 1024) return fail(SW_ERR_UNSUPPORTED);
     // decode tables: problems sorted by phase count (descending); phase p holds a prefix

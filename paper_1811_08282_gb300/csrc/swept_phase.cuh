@@ -65,10 +65,13 @@ template <class P> __host__ __device__ constexpr size_t swept_smem_elems(int W) 
 // One sub-step over row positions [lo, hi]. Radius 1: two-pass policies first
 // compute per-position intermediates on [lo-1, hi+1] into scratch, then update
 // cells. Radius 2 (flattened Euler stage): pressures, ratios, faces, update.
-template <class P, class GL, class GR, class AFTER>
+// `mid` runs (all threads) before the last pass, which reads the row on [lo, hi]
+// only: the row positions outside it that the earlier passes read are free again,
+// so the next level's flank inputs can be injected there without a barrier.
+template <class P, class GL, class GR, class AFTER, class MID>
 __device__ __forceinline__ void swept_level(const typename P::Params &prm, typename P::T *row, int rs,
                                             typename P::T *scr, int64_t lev, int lo, int hi, int slo, int shi,
-                                            GL ghost_l, GR ghost_r, AFTER after) {
+                                            GL ghost_l, GR ghost_r, AFTER after, MID mid) {
     const int tid = threadIdx.x, nt = blockDim.x;
     if constexpr (P::R == 2) {
         for (int s = lo - 2 + tid; s <= hi + 2; s += nt) P::pass_p(prm, row, rs, scr, s, lev);
@@ -77,6 +80,7 @@ __device__ __forceinline__ void swept_level(const typename P::Params &prm, typen
         __syncthreads();
         for (int s = lo + tid; s <= hi + 1; s += nt) P::pass_f(prm, row, rs, scr, s, lev);
         __syncthreads();
+        mid();
         for (int s = lo + tid; s <= hi; s += nt) {
             P::pass_u(prm, row, rs, scr, s, lev);
             after(s);
@@ -85,6 +89,7 @@ __device__ __forceinline__ void swept_level(const typename P::Params &prm, typen
         for (int s = lo - 1 + tid; s <= hi + 1; s += nt)
             P::pre(prm, row, rs, scr, s, lev, lo, hi, slo, shi, ghost_l(s), ghost_r(s - 1));
         __syncthreads();
+        mid();
         for (int s = lo + tid; s <= hi; s += nt) {
             P::step(prm, row, rs, scr, s, lev, ghost_l(s), ghost_r(s));
             after(s);
@@ -206,17 +211,20 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
             load_chunk(1);
             __syncthreads();
         }
-        if (P::INJECT_AHEAD && a.lower > 0) {
+        // level 1's inputs up front; later levels' inputs are injected one level ahead: after
+        // the level's update (slot policies) or before its last pass (in-place policies)
+        if (a.lower > 0) {
             inject(1);
             __syncthreads();
         }
+        constexpr bool kMidInject = !P::INJECT_AHEAD && (P::TWO_PASS || P::R == 2);
         for (int i = 1; i <= a.lower; ++i) {
             const int64_t lev = a.F - HL + i - 1;  // level read; level lev+1 written
             if (i > 1 && (i - 1) % kFlankChunk == 0) {  // the previous level ended with a barrier
                 load_chunk(i);
                 __syncthreads();
             }
-            if (!P::INJECT_AHEAD) {
+            if (!P::INJECT_AHEAD && !kMidInject && i > 1) {
                 inject(i);
                 __syncthreads();
             }
@@ -225,10 +233,15 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
             if (lo < slo) lo = slo;
             if (hi > shi) hi = shi;
             const bool last = (i == a.lower);
-            swept_level<P>(prm, row, rs, scr, lev, lo, hi, slo, shi, ghost_l, ghost_r, [&](int s) {
-                if (i == HL) publish_full(s, lev + 1);  // full level F reached
-                if (last && a.write_lower) P::store_state(row, rs, s, lev + 1, a.state, n, cell(s));
-            });
+            swept_level<P>(
+                prm, row, rs, scr, lev, lo, hi, slo, shi, ghost_l, ghost_r,
+                [&](int s) {
+                    if (i == HL) publish_full(s, lev + 1);  // full level F reached
+                    if (last && a.write_lower) P::store_state(row, rs, s, lev + 1, a.state, n, cell(s));
+                },
+                [&] {
+                    if (kMidInject && i < a.lower) inject(i + 1);
+                });
             if (P::INJECT_AHEAD && i < a.lower) inject(i + 1);
             __syncthreads();
         }
@@ -243,11 +256,14 @@ __device__ __forceinline__ void swept_structure(const PhaseArgs<typename P::T> &
         if (lo < slo) lo = slo;
         if (hi > shi) hi = shi;
         const bool last = (i == a.upper);
-        swept_level<P>(prm, row, rs, scr, lev, lo, hi, slo, shi, ghost_l, ghost_r, [&](int s) {
-            if (s >= el && s < el + R2) publish(s, lev + 1, 0, R2 * i + (s - el));
-            if (s >= er && s < er + R2) publish(s, lev + 1, 1, R2 * i + (s - er));
-            if (last && a.write_upper) P::store_state(row, rs, s, lev + 1, a.state, n, cell(s));
-        });
+        swept_level<P>(
+            prm, row, rs, scr, lev, lo, hi, slo, shi, ghost_l, ghost_r,
+            [&](int s) {
+                if (s >= el && s < el + R2) publish(s, lev + 1, 0, R2 * i + (s - el));
+                if (s >= er && s < er + R2) publish(s, lev + 1, 1, R2 * i + (s - er));
+                if (last && a.write_upper) P::store_state(row, rs, s, lev + 1, a.state, n, cell(s));
+            },
+            [] {});
         __syncthreads();
     }
 }

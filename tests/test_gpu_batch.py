@@ -25,21 +25,22 @@ def _lib():
     ensure_lib()
 
 
-def _problem(item, prec, W):
+def _problem(item, prec, W, flags=0):
     if item.scheme == "heat":
         return S.Problem(scheme=S.SW_HEAT, precision=prec, boundary=S.SW_PERIODIC, method=S.SW_SWEPT,
                          n=item.n, r=item.r, tile_width=W)
     return S.Problem(scheme=S.SW_EULER, precision=prec, boundary=S.SW_TRANSMISSIVE, method=S.SW_SWEPT,
-                     n=item.n, dt_dx=I.riemann_lambda(), gamma=I.GAMMA, tile_width=W)
+                     n=item.n, dt_dx=I.riemann_lambda(), gamma=I.GAMMA, tile_width=W, flags=flags)
 
 
-def _setup(prec, count=24, seed=5, hi_exp=14.0):
+def _setup(prec, count=24, seed=5, hi_exp=14.0, flat_every=0):
     import torch
     items = I.batch_problems(count, seed, lo_exp=10.0, hi_exp=hi_exp)
     probs, states, init = [], [], []
     for i, it in enumerate(items):
         W = WIDTHS[i % len(WIDTHS)]  # n is a multiple of 256 and >= 1024
-        p = _problem(it, prec, W)
+        flags = S.SW_FLAG_FLATTENED if flat_every and i % flat_every == 0 else 0
+        p = _problem(it, prec, W, flags)
         x = torch.as_tensor(it.planes.reshape(-1), device="cuda")
         probs.append(p)
         states.append(S.to_state(p, x))
@@ -52,10 +53,12 @@ def _read(probs, states):
 
 
 @pytest.mark.parametrize("prec", [S.SW_FP64, S.SW_FP32, S.SW_FP32_COMP])
-def test_batch_equals_individual_runs(prec):
+@pytest.mark.parametrize("flat_every", [0, 2])
+def test_batch_equals_individual_runs(prec, flat_every):
+    # flat_every = 2: every other problem in the flattened Euler form (heat ignores it)
     import torch
     nsteps = 150
-    items, probs, states, init = _setup(prec)
+    items, probs, states, init = _setup(prec, flat_every=flat_every)
     with S.Batch(probs, states, nsteps) as b:
         assert b.sw_batch_items() > 0
         b.sw_batch_run()
