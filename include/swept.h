@@ -76,6 +76,7 @@ extern "C" {
 #define SW_ERR_NONPHYSICAL (-5)  /* Euler: rho <= 0, p <= 0 or NaN found */
 #define SW_ERR_UNSUPPORTED (-6)
 #define SW_ERR_TOO_LARGE (-7)    /* sw_run_noalloc: needs more than SW_NOALLOC_SCRATCH_BYTES */
+#define SW_ERR_CORRUPT (-8)      /* a guard word after a scratch buffer was overwritten */
 
 #define SW_NOALLOC_SCRATCH_BYTES (16u << 20)
 
@@ -196,8 +197,19 @@ SW_API int sw_conservation(sw_handle *h, const void *state, double *sums_host, v
  * offending cell index is written to *cell (if non-NULL), else -1. */
 SW_API int sw_check_physical(sw_handle *h, const void *state, int64_t *cell, void *stream);
 
-/* Synchronise `stream` and return the latched device status (then clear it). */
+/* Synchronise `stream` and return the latched device status (then clear it).
+ * It also checks the guard words that follow each of the handle's scratch
+ * buffers (flank buffers, per-step planes: 256 bytes of a fixed pattern written
+ * at sw_create): if any changed, a kernel wrote past its buffer, and the call
+ * returns SW_ERR_CORRUPT (the guards are rewritten, so the next call reports only
+ * new damage). */
 SW_API int sw_sync_status(sw_handle *h, void *stream);
+
+/* Test hook: overwrite one byte of the guard after scratch buffer `which` (0, 1:
+ * flank buffers; 2: per-step planes) from the host, so that tests can check the
+ * detection in sw_sync_status without any kernel writing out of bounds.
+ * SW_ERR_BAD_ARG when the handle has no such buffer. */
+SW_API int sw_debug_corrupt_guard(sw_handle *h, int32_t which);
 
 /* Number of kernel launches the last sw_run on this handle issued. */
 SW_API int64_t sw_last_launch_count(const sw_handle *h);

@@ -125,6 +125,8 @@ struct sw_handle {
 namespace {
 
 constexpr int kRedBlocks = 1024;
+constexpr size_t kGuardBytes = 256;     // guard after each scratch buffer
+constexpr unsigned char kGuardByte = 0xA5;
 constexpr int kRedThreads = 256;
 
 int scheme_nv(const sw_problem &p) { return p.scheme == SW_HEAT ? 1 : 3; }
@@ -589,6 +591,7 @@ const char *sw_status_string(int s) {
     case SW_ERR_TIMEOUT: return "device-side wait timed out";
     case SW_ERR_NONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or NaN)";
     case SW_ERR_UNSUPPORTED: return "unsupported configuration";
+    case SW_ERR_CORRUPT: return "a guard word after a scratch buffer was overwritten (out-of-bounds write)";
     case SW_ERR_TOO_LARGE:
         return "problem needs more flank scratch than the static no-allocation buffer holds "
                "(SW_NOALLOC_SCRATCH_BYTES)";
@@ -676,13 +679,17 @@ int sw_create(const sw_problem *p, sw_handle **out) {
         if (h->smem > 227 * 1024) return fail(SW_ERR_UNSUPPORTED);
         h->flank_bytes = size_t(h->nsnap) * size_t(h->S) * 2 * h->W * h->esize;
         for (int i = 0; i < 2; ++i) {
-            e = cudaMalloc(&h->flank[i], h->flank_bytes);
+            e = cudaMalloc(&h->flank[i], h->flank_bytes + kGuardBytes);
+            if (e == cudaSuccess)
+                e = cudaMemset(static_cast<char *>(h->flank[i]) + h->flank_bytes, kGuardByte, kGuardBytes);
             if (e != cudaSuccess) return fail(cuda_status(e));
         }
     } else {
         if (p->scheme == SW_HEAT) h->scratch_bytes = size_t(h->nio) * p->n * h->esize;
         else h->scratch_bytes = size_t(4) * p->n * h->esize;  // Q* planes, ratio plane (lengthened form)
-        e = cudaMalloc(&h->scratch, h->scratch_bytes);
+        e = cudaMalloc(&h->scratch, h->scratch_bytes + kGuardBytes);
+        if (e == cudaSuccess)
+            e = cudaMemset(static_cast<char *>(h->scratch) + h->scratch_bytes, kGuardByte, kGuardBytes);
         if (e != cudaSuccess) return fail(cuda_status(e));
     }
     e = cudaMalloc(&h->d_status, 4 * sizeof(int));
@@ -970,7 +977,32 @@ int sw_sync_status(sw_handle *h, void *stream) {
     e = cudaMemcpy(&code, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_status(e);
     if (code != 0) cudaMemset(h->d_status, 0, sizeof(int));
+    // guards after the scratch buffers
+    void *bufs[3] = {h->flank[0], h->flank[1], h->scratch};
+    const size_t ends[3] = {h->flank_bytes, h->flank_bytes, h->scratch_bytes};
+    unsigned char g[kGuardBytes];
+    for (int i = 0; i < 3; ++i) {
+        if (!bufs[i]) continue;
+        char *at = static_cast<char *>(bufs[i]) + ends[i];
+        e = cudaMemcpy(g, at, kGuardBytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_status(e);
+        for (size_t k = 0; k < kGuardBytes; ++k) {
+            if (g[k] != kGuardByte) {
+                cudaMemset(at, kGuardByte, kGuardBytes);
+                if (code == 0) code = SW_ERR_CORRUPT;
+                break;
+            }
+        }
+    }
     return code;
+}
+
+int sw_debug_corrupt_guard(sw_handle *h, int32_t which) {
+    if (!h || which < 0 || which > 2) return SW_ERR_BAD_ARG;
+    void *buf = which < 2 ? h->flank[which] : h->scratch;
+    if (!buf) return SW_ERR_BAD_ARG;
+    const size_t end = which < 2 ? h->flank_bytes : h->scratch_bytes;
+    return cuda_status(cudaMemset(static_cast<char *>(buf) + end + 17, 0x00, 1));
 }
 
 }  // extern "C"

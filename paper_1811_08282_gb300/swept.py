@@ -23,6 +23,7 @@ SW_OK, SW_WARN_UNSTABLE = 0, 1
 SW_ERR_BAD_ARG, SW_ERR_CUDA, SW_ERR_OOM = -1, -2, -3
 SW_ERR_TIMEOUT, SW_ERR_NONPHYSICAL, SW_ERR_UNSUPPORTED = -4, -5, -6
 SW_ERR_TOO_LARGE = -7
+SW_ERR_CORRUPT = -8
 SW_NOALLOC_SCRATCH_BYTES = 16 << 20
 SW_MIN_TILE, SW_MAX_TILE = 4, 1024
 SW_FLAG_GENERIC = 1
@@ -38,7 +39,7 @@ EXPORTS = (
     "sw_last_launch_count", "sw_tile_width", "sw_status_string", "sw_abi_version",
     "sw_set_timing", "sw_launch_times", "sw_run_noalloc",
     "sw_batch_create", "sw_batch_run", "sw_batch_status", "sw_batch_items", "sw_batch_debug",
-    "sw_batch_destroy", "sw_autotune", "sw_hybrid_split", "sw_run_hybrid",
+    "sw_batch_destroy", "sw_autotune", "sw_hybrid_split", "sw_run_hybrid", "sw_debug_corrupt_guard",
 )
 
 
@@ -86,6 +87,7 @@ def load(path: str = LIB_PATH):
         "sw_run_host": ([vp, vp, vp, i64, vp], ctypes.c_int),
         "sw_hybrid_split": ([i64, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
         "sw_run_hybrid": ([vp, vp, i64, i32, i32, vp], ctypes.c_int),
+        "sw_debug_corrupt_guard": ([vp, i32], ctypes.c_int),
         "sw_pack_fp64": ([P, vp, vp, vp], ctypes.c_int),
         "sw_unpack_fp64": ([P, vp, vp, vp], ctypes.c_int),
         "sw_conservation": ([vp, vp, ctypes.POINTER(dbl), vp], ctypes.c_int),
@@ -245,6 +247,10 @@ class Handle:
         """Swept run shared with `cpu_threads` host threads (GPU work factor `work_factor`)."""
         _check(load().sw_run_hybrid(self._h, _ptr(state), int(nsteps), int(work_factor), int(cpu_threads),
                                     _stream(stream)), "sw_run_hybrid")
+
+    def sw_debug_corrupt_guard(self, which: int) -> None:
+        """Test hook: overwrite a guard byte after scratch buffer `which` (0, 1 flanks; 2 per-step)."""
+        _check(load().sw_debug_corrupt_guard(self._h, int(which)), "sw_debug_corrupt_guard")
 
     def sw_conservation(self, state, stream=None):
         sums = (ctypes.c_double * 3)()
