@@ -31,6 +31,7 @@ def main(argv=None):
     ap.add_argument("--r", type=float, default=0.3)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--generic", action="store_true", help="force the generic phase kernel (SW_FLAG_GENERIC)")
+    ap.add_argument("--flags", type=int, default=0, help="further SW_FLAG_* bits (e.g. 8: flattened Euler)")
     a = ap.parse_args(argv)
 
     import torch
@@ -43,7 +44,7 @@ def main(argv=None):
                   method=S.SW_SWEPT if a.method == "swept" else S.SW_PERSTEP, n=a.n, r=a.r,
                   dt_dx=(I.sod_lambda() if a.init == "sod" else I.riemann_lambda()), gamma=I.GAMMA,
                   tile_width=a.width if a.method == "swept" else 0,
-                  flags=S.SW_FLAG_GENERIC if a.generic else 0)
+                  flags=(S.SW_FLAG_GENERIC if a.generic else 0) | a.flags)
     if heat:
         x = I.heat_initial(I.heat_modes(a.n, 32, seed=1))
     elif a.init == "sod":
@@ -66,7 +67,7 @@ def main(argv=None):
         launches = h.sw_last_launch_count()
         rc = h.sw_sync_status()
     print(json.dumps({"scheme": a.scheme, "precision": a.precision, "method": a.method, "n": a.n,
-                      "steps": a.steps, "width": a.width, "generic": a.generic, "launches": launches, "seconds": t,
+                      "steps": a.steps, "width": a.width, "generic": a.generic, "flags": a.flags, "launches": launches, "seconds": t,
                       "gcell_updates_per_s": a.n * a.steps / t / 1e9, "status": rc}))
     return 0 if rc == 0 else 1
 
