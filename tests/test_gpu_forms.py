@@ -78,3 +78,16 @@ def test_flattened_launch_count():
     with S.Handle(p) as h:
         h.sw_run(st, 10)
         assert h.sw_last_launch_count() == 40
+
+
+@pytest.mark.parametrize("flags,W,shift", [(0, 64, 37), (S.SW_FLAG_FLATTENED, 64, 37), (S.SW_FLAG_FLATTENED, 128, 6),
+                                           (0, 256, 130)])
+def test_translation_invariance_across_seams_bitwise(flags, W, shift):
+    # periodic: shifting the initial state by s cells (s not a multiple of W) shifts the result
+    # by s, bitwise -- every cell sits at a different place in its tile, so this pins the seams
+    n, steps = 2048, 97
+    q0, lam = _init("riemann", n, seed=11)
+    p = _prob(n, W, lam, S.SW_PERIODIC, S.SW_SWEPT, S.SW_FP32, flags)
+    a = run_gpu(p, q0, steps)
+    b = run_gpu(p, np.roll(q0, shift, axis=1), steps)
+    assert np.array_equal(np.roll(a, shift, axis=1), b)
