@@ -7,6 +7,8 @@
  *   Section 4.1 / Fig. 1:  Up Triangle, Communication, Diamond, Down Triangle.
  *   Section 4.2:           the problem statement (grid size, block size, scheme)
  *                          and the two test equations.
+ *   Section 4.2, Eq. 1:    the GPU work factor of the CPU/GPU split
+ *                          (sw_run_hybrid).
  *   Section 4.3 / Fig. 2:  per-step ("Classic") decomposition, flattening and
  *                          lengthening; the 7-value Euler state per point.
  *

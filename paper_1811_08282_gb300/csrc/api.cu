@@ -1,8 +1,11 @@
 // api.cu -- C ABI of libswept.so (declared in include/swept.h): problem
-// validation, scratch ownership, the host-side phase planner of the swept rule
-// (Section 4.1) and the per-step loop (Section 4.3), plus conversion,
-// conservation and positivity utilities. All compute runs in the kernels of
-// swept_phase.cuh and perstep.cuh; this file only plans and launches.
+// validation, scratch ownership (with guard words), the host-side phase planner
+// of the swept rule (Section 4.1: generic, register-resident and flattened phase
+// kernels), the per-step loop (Section 4.3, both Euler forms), CUDA-graph replay
+// of a run, the hybrid CPU/GPU split of Section 4.2 (the host share runs
+// cpu_phase.h on a thread pool), plus conversion, conservation and positivity
+// utilities. GPU compute runs in the kernels of swept_phase.cuh, fold_*.cuh and
+// perstep.cuh; this file plans, launches and moves the hybrid run's flank slots.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,7 +1,9 @@
 // swept_phase.cuh -- one launch = one swept phase (Section 4.1, Fig. 1) over all
 // structures (triangles / diamonds) of that phase, one CTA per structure.
 //
-// Geometry (H = W/2, tiles [tW, tW+W), level = sub-step index):
+// Geometry for a 3-point stencil (radius 1; the policy's radius R scales it: a
+// half spans H/R levels and windows change by R cells per level, see
+// swept_structure) with H = W/2, tiles [tW, tW+W), level = sub-step index:
 //   phase p has full level F = p*H and centres c = t*W + H (p even, tile centred)
 //   or c = t*W (p odd, centred on the seam between tiles t-1 and t).
 //   lower half (p >= 1): levels F-H+i, i = 1..H, cells [c-i, c+i-1]   (widening)
