@@ -408,12 +408,16 @@ int launch_perstep_heat(sw_handle *h, void *state, int64_t nsteps, cudaStream_t 
     void *bufs[2] = {state, h->scratch};
     int64_t launches = 0;
     const int cap = 152 * 16;
+    // vector width: the caller's state may start anywhere; the scratch planes are 256-byte
+    // aligned, so the state's own alignment (and n, for the second plane) decides
+    const uintptr_t align = reinterpret_cast<uintptr_t>(state);
+    const bool a16 = align % 16 == 0, a32 = align % 32 == 0;
     for (int64_t s = 0; s < nsteps; ++s) {
         void *in = bufs[s & 1], *out = bufs[(s + 1) & 1];
         trace_begin(h, launches, 3, st);
         switch (h->prob.precision) {
         case SW_FP64:
-            if (n % 2 == 0)
+            if (n % 2 == 0 && a16)
                 k_heat_step<OpsD, 2><<<grid_for(n / 2, 256, cap), 256, 0, st>>>(
                     (const double *)in, (double *)out, n, h->hp.r, periodic);
             else
@@ -421,7 +425,11 @@ int launch_perstep_heat(sw_handle *h, void *state, int64_t nsteps, cudaStream_t 
                                                                              n, h->hp.r, periodic);
             break;
         case SW_FP32:
-            if (n % 4 == 0)
+            // 32 bytes per thread and iteration keeps enough loads in flight for HBM
+            if (n % 8 == 0 && a32)
+                k_heat_step<OpsF, 8><<<grid_for(n / 8, 256, cap), 256, 0, st>>>((const float *)in, (float *)out,
+                                                                                 n, h->hp.rf, periodic);
+            else if (n % 4 == 0 && a16)
                 k_heat_step<OpsF, 4><<<grid_for(n / 4, 256, cap), 256, 0, st>>>((const float *)in, (float *)out,
                                                                                  n, h->hp.rf, periodic);
             else
@@ -429,7 +437,7 @@ int launch_perstep_heat(sw_handle *h, void *state, int64_t nsteps, cudaStream_t 
                                                                              h->hp.rf, periodic);
             break;
         default:
-            if (n % 4 == 0)
+            if (n % 4 == 0 && a16)
                 k_heat_step_comp<4><<<grid_for(n / 4, 256, cap), 256, 0, st>>>(
                     (const float *)in, (float *)out, n, h->hp.rf, h->hp.rf_lo, periodic);
             else

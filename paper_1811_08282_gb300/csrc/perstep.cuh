@@ -12,11 +12,17 @@
 
 namespace sw {
 
+// Vector types of V consecutive elements; V > 1 needs V * sizeof(T)-byte aligned
+// addresses (the launcher checks the state pointer before choosing V).
+struct alignas(32) Float8 {
+    float4 a, b;
+};
 template <class T, int V> struct VecT;
 template <> struct VecT<double, 1> { using type = double; };
 template <> struct VecT<double, 2> { using type = double2; };
 template <> struct VecT<float, 1> { using type = float; };
 template <> struct VecT<float, 4> { using type = float4; };
+template <> struct VecT<float, 8> { using type = Float8; };
 
 template <class T, int V>
 __device__ __forceinline__ void vload(const T *p, T (&v)[V]) {

@@ -189,3 +189,25 @@ def test_host_buffer_entry_point_matches_device_run():
     with S.Handle(p) as h:
         h.sw_run_host(buf.ctypes.data, out.ctypes.data, steps, 0)
     assert np.array_equal(out, dev)
+
+
+@pytest.mark.parametrize("prec,offset", [(S.SW_FP32, 1), (S.SW_FP32, 4), (S.SW_FP32, 8), (S.SW_FP64, 1),
+                                         (S.SW_FP64, 2), (S.SW_FP32_COMP, 1)])
+@pytest.mark.parametrize("steps", [7, 8])
+def test_perstep_on_any_state_alignment(prec, offset, steps):
+    # the caller's state may start at any element: the per-step kernel picks its vector
+    # width from the pointer's alignment, and every width gives the same bits
+    import torch
+    n = 8192
+    p = S.Problem(scheme=S.SW_HEAT, precision=prec, boundary=S.SW_PERIODIC, method=S.SW_PERSTEP, n=n, r=0.3)
+    u0 = I.heat_initial(I.heat_modes(n, 8, seed=offset))
+    want = run_gpu(p, u0[None], steps)
+    st = S.to_state(p, torch.as_tensor(u0, device="cuda"))
+    big = torch.zeros(st.numel() + 16, dtype=st.dtype, device="cuda")
+    view = big[offset:offset + st.numel()]  # every plane of the layout, starting `offset` elements in
+    view.copy_(st)
+    with S.Handle(p) as h:
+        h.sw_run(view, steps)
+        assert h.sw_sync_status() == S.SW_OK
+        got = S.to_fp64(p, view.clone()).cpu().numpy().reshape(1, n)
+    assert np.array_equal(got, want)
