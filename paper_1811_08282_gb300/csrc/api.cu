@@ -437,7 +437,10 @@ int launch_perstep_heat(sw_handle *h, void *state, int64_t nsteps, cudaStream_t 
                                                                              h->hp.rf, periodic);
             break;
         default:
-            if (n % 4 == 0 && a16)
+            if (n % 8 == 0 && a32)
+                k_heat_step_comp<8><<<grid_for(n / 8, 256, cap), 256, 0, st>>>(
+                    (const float *)in, (float *)out, n, h->hp.rf, h->hp.rf_lo, periodic);
+            else if (n % 4 == 0 && a16)
                 k_heat_step_comp<4><<<grid_for(n / 4, 256, cap), 256, 0, st>>>(
                     (const float *)in, (float *)out, n, h->hp.rf, h->hp.rf_lo, periodic);
             else
