@@ -43,7 +43,9 @@
 extern "C" {
 #endif
 
-#define SW_ABI_VERSION 1
+/* 2: sw_run_hybrid / sw_hybrid_split, SW_FLAG_EULER_FOLD / LENGTHENED / FLATTENED /
+ * GRAPH, SW_ERR_CORRUPT and sw_debug_corrupt_guard. */
+#define SW_ABI_VERSION 2
 
 #if defined(__GNUC__)
 #define SW_API __attribute__((visibility("default")))

@@ -15,6 +15,7 @@ from dataclasses import dataclass
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libswept.so")
 
+ABI_VERSION = 2  # SW_ABI_VERSION of include/swept.h
 SW_HEAT, SW_EULER = 0, 1
 SW_FP64, SW_FP32, SW_FP32_COMP = 0, 1, 2
 SW_PERIODIC, SW_TRANSMISSIVE = 0, 1
@@ -112,6 +113,9 @@ def load(path: str = LIB_PATH):
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = res
+    if lib.sw_abi_version() != ABI_VERSION:
+        raise RuntimeError(f"libswept.so at {path} has ABI version {lib.sw_abi_version()}, this binding "
+                           f"expects {ABI_VERSION}: rebuild it with `python -m paper_1811_08282_gb300.build`")
     _lib = lib
     return lib
 
