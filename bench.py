@@ -47,6 +47,12 @@ FLOPS_PER_UPDATE = 5  # a + b, fma(-2, u, .), fma(r, ., u): 1 add + 2 FMA
 # FP64 peak: 152 SMs x 2 FP64 FMA / clock / SM x 2 flop x 2.07 GHz (the GB300
 # part's 1.25 TFLOP/s dense FP64 at its maximum SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# The FP64 heat kernels run half their cells on the integer pipes (the same bits), so
+# their ceiling is set by two pipes: the FP64 pipe (2 instructions / clock / SM) and
+# the integer ALU pipe (64 lanes / clock / SM), each divided by the instructions per
+# update it carries (counted by ncu, recorded with the kernel's source hash).
+FP64_INST_PER_S = 152 * 2 * 2.07e9
+ALU_LANE_INST_PER_S = 152 * 64 * 2.07e9
 
 
 def parse():
@@ -79,7 +85,7 @@ def initial_state():
 
 # sources that define each timed kernel (a recorded traffic figure is void once they change)
 KERNEL_SOURCES = {
-    "k_heat_fold": ("common.cuh", "heat.cuh", "flanks.cuh", "fold_heat.cuh"),
+    "k_heat_fold": ("common.cuh", "heat.cuh", "flanks.cuh", "fp64_soft.cuh", "fold_heat.cuh"),
     "k_swept_phase": ("common.cuh", "heat.cuh", "heat_policy.cuh", "flanks.cuh", "swept_phase.cuh"),
 }
 
@@ -93,8 +99,9 @@ def kernel_source_sha(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, key: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+def recorded(kernel: str, key: str, field: str = "bytes_per_launch"):
+    """A figure from the committed ncu summaries (DRAM bytes per launch, instructions
+    per update), if the kernel is unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -105,9 +112,13 @@ def recorded_traffic(kernel: str, key: str):
             continue
         k, v = line.split("=", 1)
         vals[k.strip()] = v.strip()
-    if vals.get(f"{kernel}.source_sha") != kernel_source_sha(kernel) or f"{key}.bytes_per_launch" not in vals:
+    if vals.get(f"{kernel}.source_sha") != kernel_source_sha(kernel) or f"{key}.{field}" not in vals:
         return None
-    return float(vals[f"{key}.bytes_per_launch"])
+    return float(vals[f"{key}.{field}"])
+
+
+def recorded_traffic(kernel: str, key: str):
+    return recorded(kernel, key, "bytes_per_launch")
 
 
 # ------------------------------------------------------------------ clocks
@@ -279,14 +290,29 @@ def run_ours(args):
     fold = best_w in (128, 256, 512, 1024)
     kname = "k_heat_fold" if fold else "k_swept_phase"
     traffic = recorded_traffic(kname, f"{kname}.heat_fp64.n2^24")
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": traffic,
+    # the register-resident kernel at W = 128 / 256 puts every other cell on the integer
+    # pipes: its ceiling is the busier of the FP64 and ALU pipes for its instruction mix
+    peak, peak_source = FP64_PEAK_TFLOPS, \
+        "FP64 1.25 TFLOP/s class: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz (nominal, recipe)"
+    fp64_ipu = recorded(kname, f"{kname}.heat_fp64.w{best_w}", "fp64_inst_per_update") if fold else None
+    alu_ipu = recorded(kname, f"{kname}.heat_fp64.w{best_w}", "alu_inst_per_update") if fold else None
+    if fp64_ipu and alu_ipu:
+        ceiling = min(FP64_INST_PER_S / fp64_ipu, ALU_LANE_INST_PER_S / alu_ipu)  # updates/s
+        peak = ceiling * FLOPS_PER_UPDATE / 1e12
+        peak_source = (f"pipe ceiling of the FP64 + integer-pipe kernel, in FP64-equivalent flops (5 per update): "
+                       f"min(FP64 pipe 152 SM x 2/clk x 2.07 GHz / {fp64_ipu:.3f} FP64 instr per update, "
+                       f"ALU pipe 152 SM x 64 lanes/clk x 2.07 GHz / {alu_ipu:.2f} ALU instr per update) "
+                       f"= {ceiling / 1e9:.1f} G updates/s (instruction counts: ncu, profiles/traffic.txt)")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "fp64_pipe_peak": FP64_PEAK_TFLOPS,
+                "frac_of_fp64_pipe_peak": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
                 "kernel": (f"k_heat_fold<{best_w // 32}, FoldF64> (Diamond phases)" if fold
                            else "k_swept_phase<HeatPolicy<FP64>> (Diamond phases)"),
                 "launches_traced": len(diamonds),
                 "avg_launch_ms": statistics.mean(diamonds) if diamonds else None,
                 "flops_per_launch": flops_per_launch,
-                "peak_source": "FP64 1.25 TFLOP/s class: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz (nominal, recipe)"}
+                "peak_source": peak_source}
 
     # 3) end to end through the C ABI with host buffers (H2D + run + D2H inside the region)
     host_in = torch.empty(N, dtype=torch.float64, pin_memory=True)

@@ -408,6 +408,7 @@ int launch_perstep_heat(sw_handle *h, void *state, int64_t nsteps, cudaStream_t 
     void *bufs[2] = {state, h->scratch};
     int64_t launches = 0;
     const int cap = 152 * 16;
+    constexpr int64_t kMixedMinCells = int64_t(1) << 21;  // ~7 waves of 152 x 2048 threads at 1 cell each
     // vector width: the caller's state may start anywhere; the scratch planes are 256-byte
     // aligned, so the state's own alignment (and n, for the second plane) decides
     const uintptr_t align = reinterpret_cast<uintptr_t>(state);
@@ -417,7 +418,13 @@ int launch_perstep_heat(sw_handle *h, void *state, int64_t nsteps, cudaStream_t 
         trace_begin(h, launches, 3, st);
         switch (h->prob.precision) {
         case SW_FP64:
-            if (n % 2 == 0 && a16)
+            // large grids: four (or two) cells per thread, half of them on the integer
+            // pipes; a smaller grid is latency-bound, and one cell per thread on the FP64
+            // pipe keeps the dependent chains short
+            if (n >= kMixedMinCells && n % 4 == 0 && a32)
+                k_heat_step<OpsD, 4><<<grid_for(n / 4, 256, cap), 256, 0, st>>>(
+                    (const double *)in, (double *)out, n, h->hp.r, periodic);
+            else if (n >= kMixedMinCells && n % 2 == 0 && a16)
                 k_heat_step<OpsD, 2><<<grid_for(n / 2, 256, cap), 256, 0, st>>>(
                     (const double *)in, (double *)out, n, h->hp.r, periodic);
             else

@@ -13,11 +13,13 @@ bool fold_supported(int precision, int W) {
 
 // Measured on GB300 at N = 2^24 (diamond phases, 4-warp CTAs; multiples of 4 keep
 // the SMs evenly loaded): FP32 peaks at 24 warps/SM up to W = 512, 12 at W = 1024;
-// FP32 hi/lo at 24 (W = 128), 16 (256), 12 (512); FP64 at 8.
+// FP32 hi/lo at 24 (W = 128), 16 (256), 12 (512). FP64 with half the cells on the
+// integer pipes wants more warps in flight: 32 at W = 128, 16 at W = 256; the
+// FP64-only widths (512, 1024) peak at 8.
 int fold_warps_per_sm(int precision, int W) {
     if (precision == SW_FP32) return W >= 1024 ? 12 : 24;
     if (precision == SW_FP32_COMP) return W <= 128 ? 24 : (W == 256 ? 16 : (W == 512 ? 12 : 8));
-    return 8;
+    return W <= 128 ? 32 : (W == 256 ? 16 : 8);
 }
 
 template <int K, class C>

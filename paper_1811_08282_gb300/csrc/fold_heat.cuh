@@ -20,22 +20,31 @@
 // the two kernels mix freely within one run (the generic kernel does the Up
 // and Down triangles and any truncated phase), and the per-cell update is the
 // same function, so results are bitwise identical.
+//
+// FP64: every other register slot evaluates the update with integer arithmetic
+// (fp64_soft.cuh, the same bits), so that the FP64 pipe -- two operations per SM
+// per clock on GB300 -- and the integer pipes each carry half the cells.
 #pragma once
 #include "flanks.cuh"
+#include "fp64_soft.cuh"
 #include "heat.cuh"
 
 namespace sw {
 
 // Cell policies: value type, update and warp shuffle.
+// SOFT_EVERY = s > 0: register slot j with j % s == s - 1 is updated on the integer
+// pipes (soft64::heat_update) instead of the FP64 pipe, with the same bits.
 struct FoldF32 {
     using T = float;
     using V = float;
     static constexpr int NSNAP = 1;
+    static constexpr int SOFT_EVERY = 0;
     static __device__ __forceinline__ V upd(const HeatParams &p, V a, V u, V b) {
         return heat_update<OpsF>(p.rf, a, u, b);
     }
     static __device__ __forceinline__ V shfl(V x, int src) { return __shfl_sync(0xffffffffu, x, src); }
     static __device__ __forceinline__ V zero() { return 0.f; }
+    static __device__ __forceinline__ V idle() { return 0.f; }
     static __device__ __forceinline__ V load(const T *p, int64_t plane, int64_t i) { return p[i]; }
     static __device__ __forceinline__ void store(T *p, int64_t plane, int64_t i, V x) { p[i] = x; }
 };
@@ -44,11 +53,18 @@ struct FoldF64 {
     using T = double;
     using V = double;
     static constexpr int NSNAP = 1;
+    static constexpr int SOFT_EVERY = 2;  // half the cells on the integer pipes
     static __device__ __forceinline__ V upd(const HeatParams &p, V a, V u, V b) {
         return heat_update<OpsD>(p.r, a, u, b);
     }
+    static __device__ __forceinline__ V upd_soft(const soft64::HeatR &h, V a, V u, V b, bool &ok) {
+        return soft64::value(soft64::heat_update(h, soft64::bits(a), soft64::bits(u), soft64::bits(b), ok));
+    }
     static __device__ __forceinline__ V shfl(V x, int src) { return __shfl_sync(0xffffffffu, x, src); }
     static __device__ __forceinline__ V zero() { return 0.0; }
+    // register cells outside the live region are updated and never read; 1.0 keeps
+    // them on the integer path (a zero would send the warp to the FP64 fallback)
+    static __device__ __forceinline__ V idle() { return 1.0; }
     static __device__ __forceinline__ V load(const T *p, int64_t plane, int64_t i) { return p[i]; }
     static __device__ __forceinline__ void store(T *p, int64_t plane, int64_t i, V x) { p[i] = x; }
 };
@@ -57,6 +73,7 @@ struct FoldComp {
     using T = float;
     using V = HL;
     static constexpr int NSNAP = 2;  // flank planes: high parts, low parts
+    static constexpr int SOFT_EVERY = 0;
     static __device__ __forceinline__ V upd(const HeatParams &p, V a, V u, V b) {
         return heat_update_comp(p.rf, p.rf_lo, a, u, b);
     }
@@ -64,6 +81,7 @@ struct FoldComp {
         return HL{__shfl_sync(0xffffffffu, x.h, src), __shfl_sync(0xffffffffu, x.l, src)};
     }
     static __device__ __forceinline__ V zero() { return HL{0.f, 0.f}; }
+    static __device__ __forceinline__ V idle() { return HL{0.f, 0.f}; }
     static __device__ __forceinline__ V load(const T *p, int64_t plane, int64_t i) {
         return HL{p[i], p[plane + i]};
     }
@@ -127,9 +145,15 @@ __global__ void __launch_bounds__(128) k_heat_fold(FoldArgs<typename C::T> a, He
     const bool up = a.p == 0;
     const int imax = up ? a.upper : (a.lower > a.upper ? a.lower : a.upper);
 
+    // integer-pipe slots (up to K = 8: beyond, the extra registers spill): r
+    // unpacked once (an r outside its range fails every soft update, which then
+    // runs on the FP64 pipe)
+    constexpr int SOFT = K <= 8 ? C::SOFT_EVERY : 0;
+    soft64::HeatR hr{};
+    if constexpr (SOFT > 0) hr = soft64::make_heat_r(prm.r);
     V v[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) v[j] = C::zero();
+    for (int j = 0; j < K; ++j) v[j] = C::idle();
     int shift = 0;  // lanes by which the finishing diamond's frame is rotated (0 or 16)
 
     // Up Triangle: no pairing (two full rows cannot share the window); the iteration
@@ -220,6 +244,9 @@ __global__ void __launch_bounds__(128) k_heat_fold(FoldArgs<typename C::T> a, He
                 const bool pC = Lact && lane == ((g + shift) & 31);
                 const bool pD = Lact && !first && lane == ((((u == 0) ? g - 1 : g) + shift + 32) & 31);
                 V nv[K];
+                V xs[K], cs[K], ys[K];  // inputs of the integer-pipe slots, for a fallback
+                bool oks[K];
+                bool okall = true;
 #pragma unroll
                 for (int j = 0; j < K; ++j) {
                     V x = (j == 0) ? left_in : v[j - 1];
@@ -237,7 +264,26 @@ __global__ void __launch_bounds__(128) k_heat_fold(FoldArgs<typename C::T> a, He
                         if (first) x = pC ? fl1 : x;
                     }
                     if (j == sD) y = pD ? fr0 : y;
+                    if constexpr (SOFT > 0) {
+                        if (j % SOFT == SOFT - 1) {
+                            nv[j] = C::upd_soft(hr, x, c, y, oks[j]);
+                            okall = okall && oks[j] && hr.usable;
+                            xs[j] = x;
+                            cs[j] = c;
+                            ys[j] = y;
+                            continue;
+                        }
+                    }
                     nv[j] = C::upd(prm, x, c, y);
+                }
+                if constexpr (SOFT > 0) {
+                    // rare (a neighbour far from u in magnitude, a zero): the whole warp
+                    // branches, and the flagged cells are updated on the FP64 pipe
+                    if (__any_sync(0xffffffffu, !okall)) {
+#pragma unroll
+                        for (int j = SOFT - 1; j < K; j += SOFT)
+                            if (!(oks[j] && hr.usable)) nv[j] = soft64::heat_update_fp64(prm.r, xs[j], cs[j], ys[j]);
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < K; ++j) v[j] = nv[j];

@@ -8,6 +8,9 @@
 // memory and evaluates each face flux once. Both call the same per-cell
 // functions as the swept phases, so the two decompositions agree bitwise.
 #pragma once
+#include <type_traits>
+
+#include "fp64_soft.cuh"
 #include "schemes.cuh"
 
 namespace sw {
@@ -17,9 +20,13 @@ namespace sw {
 struct alignas(32) Float8 {
     float4 a, b;
 };
+struct alignas(32) Double4 {
+    double2 a, b;
+};
 template <class T, int V> struct VecT;
 template <> struct VecT<double, 1> { using type = double; };
 template <> struct VecT<double, 2> { using type = double2; };
+template <> struct VecT<double, 4> { using type = Double4; };
 template <> struct VecT<float, 1> { using type = float; };
 template <> struct VecT<float, 4> { using type = float4; };
 template <> struct VecT<float, 8> { using type = Float8; };
@@ -55,6 +62,11 @@ __global__ void __launch_bounds__(256) k_heat_step(const typename O::T *__restri
                                                    typename O::T *__restrict__ out, int64_t n,
                                                    typename O::T r, int periodic) {
     using T = typename O::T;
+    // FP64 with two or more cells per thread: the odd cells are updated on the
+    // integer pipes (soft64::heat_update, the same bits) beside the FP64 pipe
+    constexpr bool SOFT = std::is_same<T, double>::value && V >= 2;
+    soft64::HeatR hr{};
+    if constexpr (SOFT) hr = soft64::make_heat_r((double)r);
     const int64_t nch = n / V;
     const int64_t nch_r = (nch + 31) & ~int64_t(31);
     const int lane = threadIdx.x & 31;
@@ -74,11 +86,29 @@ __global__ void __launch_bounds__(256) k_heat_step(const typename O::T *__restri
             if (lane == 0) left = in[nb_index(j0 - 1, n, periodic)];
             if (lane == 31 || ch + 1 >= nch) right = in[nb_index(j0 + V, n, periodic)];
             T o[V];
+            bool okall = true;
 #pragma unroll
             for (int k = 0; k < V; ++k) {
                 const T a = (k == 0) ? left : v[k - 1];
                 const T b = (k == V - 1) ? right : v[k + 1];
+                if constexpr (SOFT) {
+                    if (k & 1) {
+                        bool ok;
+                        o[k] = soft64::value(soft64::heat_update(hr, soft64::bits(a), soft64::bits(v[k]),
+                                                                 soft64::bits(b), ok));
+                        okall = okall && ok && hr.usable;
+                        continue;
+                    }
+                }
                 o[k] = heat_update<O>(r, a, v[k], b);
+            }
+            if constexpr (SOFT) {
+                if (__any_sync(__activemask(), !okall)) {
+                    // some cell left the integer path's range: odd slots on the FP64 pipe
+#pragma unroll
+                    for (int k = 1; k < V; k += 2)
+                        o[k] = soft64::heat_update_fp64((double)r, v[k - 1], v[k], (k == V - 1) ? right : v[k + 1]);
+                }
             }
             vstore<T, V>(out + j0, o);
         }

@@ -89,10 +89,13 @@ def test_fp32_variants_swept_equals_perstep(prec, tol, n, W, steps, bc, r):
     (4096, 256, 129),
     (4096, 256, 640),        # a multiple of W/2: complete Down Triangle
     (8192, 512, 256 * 7 + 5),
+    (1 << 21, 128, 200),     # FP64: a smooth field, integer path nearly everywhere
 ])
 def test_register_diamond_kernel_matches_generic_kernel(prec, n, W, steps):
     # periodic heat at W = 32K uses the register-resident Diamond kernel for every complete
-    # Diamond phase; SW_FLAG_GENERIC forces the shared-memory kernel everywhere
+    # Diamond phase; SW_FLAG_GENERIC forces the shared-memory kernel everywhere. FP64 at
+    # W = 128 and 256 updates half the register cells on the integer pipes, the generic
+    # kernel all of them on the FP64 pipe: the two must agree bit for bit
     u0 = _init(n, seed=W + steps)
     fast = run_gpu(_prob(n, W, 0.33, S.SW_PERIODIC, S.SW_SWEPT, prec), u0[None], steps)
     gen = run_gpu(_prob(n, W, 0.33, S.SW_PERIODIC, S.SW_SWEPT, prec, flags=S.SW_FLAG_GENERIC), u0[None], steps)
@@ -191,14 +194,16 @@ def test_host_buffer_entry_point_matches_device_run():
     assert np.array_equal(out, dev)
 
 
-@pytest.mark.parametrize("prec,offset", [(S.SW_FP32, 1), (S.SW_FP32, 4), (S.SW_FP32, 8), (S.SW_FP64, 1),
-                                         (S.SW_FP64, 2), (S.SW_FP32_COMP, 1)])
+@pytest.mark.parametrize("prec,offset,n", [(S.SW_FP32, 1, 8192), (S.SW_FP32, 4, 8192), (S.SW_FP32, 8, 8192),
+                                           (S.SW_FP64, 1, 8192), (S.SW_FP64, 2, 8192), (S.SW_FP32_COMP, 1, 8192),
+                                           (S.SW_FP64, 1, 1 << 21), (S.SW_FP64, 2, 1 << 21)])
 @pytest.mark.parametrize("steps", [7, 8])
-def test_perstep_on_any_state_alignment(prec, offset, steps):
+def test_perstep_on_any_state_alignment(prec, offset, n, steps):
     # the caller's state may start at any element: the per-step kernel picks its vector
-    # width from the pointer's alignment, and every width gives the same bits
+    # width from the pointer's alignment, and every width gives the same bits. FP64 at
+    # 2^21 cells: 4 (aligned), 2 (offset 2) and 1 (offset 1) cells per thread, the first
+    # two with half the cells on the integer pipes, the last on the FP64 pipe alone
     import torch
-    n = 8192
     p = S.Problem(scheme=S.SW_HEAT, precision=prec, boundary=S.SW_PERIODIC, method=S.SW_PERSTEP, n=n, r=0.3)
     u0 = I.heat_initial(I.heat_modes(n, 8, seed=offset))
     want = run_gpu(p, u0[None], steps)
