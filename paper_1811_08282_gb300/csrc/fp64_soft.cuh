@@ -9,20 +9,21 @@
 //
 // The three neighbours of a smooth field are close in magnitude and of one sign,
 // so the update works on magnitudes in one fixed-point frame tied to u's
-// exponent eu: a value is an integer F times 2^(eu - 1082), in which u's
-// significand is shifted left by 7 bits.
+// exponent eu: a value is an integer F times 2^(eu - 1079), in which u's
+// significand is shifted left by 4 bits.
 //   1. a + b is an exact integer sum; rounding it to 53 significant bits gives
 //      RN(a + b) (the frame holds every bit of a and b whose exponents lie in
-//      [eu - 7, eu + 1]).
-//   2. s - 2u is again exact; rounding gives RN(s - 2u) = d.
+//      [eu - 4, eu + 4]).
+//   2. s - 2u is again exact, and so is RN(s - 2u) = d while |d| < 2^53 frame
+//      units, i.e. |d| < |u| / 8: a second difference that large leaves the path.
 //   3. r*d is a small correction to u: in units of ulp(u) it is
 //      k = r*d / ulp(u), an integer plus a fraction taken from the 128-bit
 //      product of r's and d's significands. RN(u + r*d) is u's bit pattern plus
 //      or minus round(k) as long as the result stays in u's binade (or lands
 //      exactly on the next power of two), where the spacing is ulp(u); an exact
 //      tie goes to the neighbour whose last bit is even.
-// Anything else -- mixed signs, operands outside the exponent window, a zero or
-// subnormal u, a result leaving u's binade, r outside [2^-26, 2^6) -- clears
+// Anything else -- mixed signs, operands outside the exponent window, |d| >= |u|/8,
+// a zero or subnormal u, a result leaving u's binade, r outside [2^-29, 2^3) -- clears
 // `ok`, and the caller evaluates the update with the FP64 instructions
 // (heat_update_fp64) instead.
 #pragma once
@@ -96,14 +97,13 @@ SW_HD uint64_t shr_small(uint64_t m, unsigned s) {
 #endif
 }
 
-// m (< 2^63 - 2^10) rounded to 53 significant bits, to nearest even. Only the
-// low word loses bits (at most 11), so the leading-zero count of the high word
-// decides the shift: a high word below 2^21 means m already fits.
+// m in [2^53, 2^63 - 2^10) rounded to 53 significant bits, to nearest even. It
+// has 1 to 10 bits below the 53rd significant one, all in the low word, so the
+// leading-zero count of the high word gives the shift.
 SW_HD uint64_t round53(uint64_t m) {
-    const int lz = clz32((uint32_t)(m >> 32));
-    const unsigned sh = lz < 11 ? (unsigned)(11 - lz) : 0u;
+    const unsigned sh = (unsigned)(11 - clz32((uint32_t)(m >> 32)));
     const uint32_t lo = (uint32_t)m;
-    const uint32_t bias = sh ? (1u << (sh - 1)) - 1u + ((lo >> sh) & 1u) : 0u;  // ties to even
+    const uint32_t bias = (1u << (sh - 1)) - 1u + ((lo >> sh) & 1u);  // ties to even
     return (m + bias) & ~(uint64_t)((1u << sh) - 1u);
 }
 
@@ -112,9 +112,9 @@ struct HeatR {
     uint64_t m11;     // r's significand << 11
     uint64_t hm1;     // 2^(c0 - 1) - 1
     uint64_t lomask;  // m11 * x has a bit set below 2^64 iff x & lomask != 0
-    unsigned c0;      // 1029 - (r's biased exponent): r*d / ulp(u) = m11 |F_d| / 2^(64 + c0)
+    unsigned c0;      // 1026 - (r's biased exponent): r*d / ulp(u) = m11 |F_d| / 2^(64 + c0)
     uint32_t neg;     // 1 if r < 0
-    bool usable;      // r normal and c0 in [1, 31]: r in [2^-26, 2^6)
+    bool usable;      // r normal and c0 in [1, 31]: r in [2^-29, 2^3)
 };
 
 SW_HD HeatR make_heat_r(double r) {
@@ -122,7 +122,7 @@ SW_HD HeatR make_heat_r(double r) {
     const int er = (int)((b >> 52) & 0x7FF);
     HeatR h;
     h.m11 = ((b & kFrac) | kHidden) << 11;
-    const int c0 = 1029 - er;
+    const int c0 = 1026 - er;
     h.usable = er != 0 && c0 >= 1 && c0 <= 31;
     h.c0 = h.usable ? (unsigned)c0 : 1u;
     h.hm1 = (1ull << (h.c0 - 1)) - 1u;
@@ -142,18 +142,19 @@ SW_HD HeatR make_heat_r(double r) {
 SW_HD uint64_t heat_update(const HeatR &r, uint64_t A, uint64_t U, uint64_t B, bool &ok) {
     const uint32_t ah = (uint32_t)(A >> 32), uh = (uint32_t)(U >> 32), bh = (uint32_t)(B >> 32);
     const int eu = (int)((uh >> 20) & 0x7FF);
-    const int da = (int)((ah >> 20) & 0x7FF) - eu + 7;
-    const int db = (int)((bh >> 20) & 0x7FF) - eu + 7;
+    const int da = (int)((ah >> 20) & 0x7FF) - eu + 4;
+    const int db = (int)((bh >> 20) & 0x7FF) - eu + 4;
     // one sign; u normal, far from overflow and underflow; a and b in
-    // [2^(eu-1030), 2^(eu-1021)): every intermediate is a normal double, frame < 2^62
+    // [2^(eu-1027), 2^(eu-1018)): every intermediate is a normal double, frame < 2^62
     ok = (((ah ^ uh) | (bh ^ uh)) >> 31) == 0 && (unsigned)(eu - 64) <= 1976u && (unsigned)da <= 8u &&
          (unsigned)db <= 8u;
     const uint64_t fa = shl_small((A & kFrac) | kHidden, (unsigned)da & 15u);
     const uint64_t fb = shl_small((B & kFrac) | kHidden, (unsigned)db & 15u);
-    const uint64_t s = round53(fa + fb);                           // |RN(a + b)|
-    const int64_t dd = (int64_t)(s - (((U & kFrac) | kHidden) << 8));  // exact (s - 2u) / sign(u)
+    const uint64_t s = round53(fa + fb);                           // |RN(a + b)|, >= 2^53
+    const int64_t dd = (int64_t)(s - (((U & kFrac) | kHidden) << 5));  // exact (s - 2u) / sign(u)
     const uint64_t dsg = (uint64_t)(dd >> 63);
-    const uint64_t dm = round53(((uint64_t)dd ^ dsg) - dsg);       // |RN(s - 2u)| = |d|
+    const uint64_t dm = ((uint64_t)dd ^ dsg) - dsg;                // |d|: exact below 2^53
+    ok = ok && (dm >> 53) == 0;
     // k = r |d| / ulp(u) = (ph + pl 2^-64) / 2^c0
     const uint64_t ph = mulhi(r.m11, dm);
     const bool plo = (dm & r.lomask) != 0;

@@ -66,11 +66,15 @@ int main(int argc, char **argv) {
         }
         report("smooth", c);
     }
-    {   // independent exponents around u's (one sign), across the edges of the exponent window
+    {   // one neighbour 2^0 .. 2^-9 of u (across the low edge of the exponent window), the
+        // other about 2u - a, so that the second difference stays small
         Count c;
         for (long i = 0; i < N; ++i) {
-            const double u = rexp(1023, 1023);
-            check(c, ur(rng), std::copysign(rexp(1014, 1026), u), u, std::copysign(rexp(1014, 1026), u));
+            const double u = rexp(1020, 1026);
+            const double a = near(std::ldexp(u, -(int)(rng() % 10)), 2);
+            const double b = near(2.0 * u - a, 20 + (int)(rng() % 30));
+            if (rng() & 1) check(c, ur(rng), a, u, b);
+            else check(c, ur(rng), b, u, a);
         }
         report("window", c);
     }

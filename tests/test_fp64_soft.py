@@ -37,7 +37,7 @@ def harness(tmp_path_factory):
 
 # family -> minimum share of cases on the integer path
 MIN_FAST = {"smooth": 0.9, "window": 0.2, "ties": 0.9, "binade": 0.5, "r_bits": 0.8, "special": 0.01,
-            "heat_run": 0.95}
+            "heat_run": 0.9}
 
 
 @pytest.mark.parametrize("seed", [1, 2])
