@@ -44,8 +44,11 @@ extern "C" {
 #endif
 
 /* 2: sw_run_hybrid / sw_hybrid_split, SW_FLAG_EULER_FOLD / LENGTHENED / FLATTENED /
- * GRAPH, SW_ERR_CORRUPT and sw_debug_corrupt_guard. */
-#define SW_ABI_VERSION 2
+ * GRAPH, SW_ERR_CORRUPT and sw_debug_corrupt_guard.
+ * 3: swept Euler runs default to the flattened form where W allows it;
+ * SW_FLAG_LENGTHENED selects the lengthened form for swept runs too; sw_autotune
+ * also picks the Euler form. */
+#define SW_ABI_VERSION 3
 
 #if defined(__GNUC__)
 #define SW_API __attribute__((visibility("default")))
@@ -96,18 +99,24 @@ extern "C" {
                                 cells per level at a lower occupancy. Ignored with
                                 SW_FLAG_GENERIC. */
 /* The two data-structure strategies of Section 4.3 (Fig. 2) for the Euler step; every
-   form gives the same bits. By default swept runs are lengthened (four 3-point
-   sub-steps per step, the pressure ratio stored between them) and per-step runs are
-   flattened (two 5-point stages per step, two launches). */
-#define SW_FLAG_LENGTHENED 4 /* per-step Euler: the lengthened form, four launches per step */
+   form gives the same bits. Lengthened: four 3-point sub-steps per step, the pressure
+   ratio stored between them. Flattened: two 5-point stages per step. Without either
+   flag, per-step runs are flattened (two launches per step) and swept runs are
+   flattened whenever the base width allows radius-2 windows (W % 4 == 0, W >= 8),
+   else lengthened; SW_FLAG_EULER_FOLD (swept) implies lengthened. The default
+   follows the measured speed: on GB300 the flattened form is the faster one for
+   both methods (fewer barriers per step, 722 against 943 thread instructions per
+   cell-step in FP32 swept). Both flags at once: SW_ERR_BAD_ARG. */
+#define SW_FLAG_LENGTHENED 4 /* Euler: the lengthened form (per-step: four launches per step) */
 #define SW_FLAG_GRAPH 16     /* sw_run captures the run's launches once into a CUDA graph
                                 (on a private stream, launch tracing off) and replays it on the
                                 caller's stream; the handle keeps one graph, for the last
                                 (state pointer, nsteps) pair, and captures again when either
                                 changes. Same results. */
-#define SW_FLAG_FLATTENED 8  /* swept Euler: the flattened form, two 5-point stages per step
-                                (windows widen and narrow by 2 cells per level, W/4 levels per
-                                phase); generic kernel only (ignores SW_FLAG_EULER_FOLD) */
+#define SW_FLAG_FLATTENED 8  /* Euler: the flattened form, two 5-point stages per step; swept:
+                                windows widen and narrow by 2 cells per level, W/4 levels per
+                                phase, W % 4 == 0 and W >= 8, generic kernel only (ignores
+                                SW_FLAG_EULER_FOLD) */
 
 #define SW_MIN_TILE 4
 #define SW_MAX_TILE 1024
@@ -125,8 +134,9 @@ typedef struct sw_problem {
     double gamma;       /* Euler: ratio of specific heats (> 1) */
     int32_t tile_width; /* swept base width W: even, SW_MIN_TILE..SW_MAX_TILE,
                            divides n; 0 selects the library default */
-    int32_t flags;      /* 0 or an OR of the SW_FLAG_* bits above (sw_run_noalloc: must be 0;
-                           batches: 0 or SW_FLAG_FLATTENED) */
+    int32_t flags;      /* 0 or an OR of the SW_FLAG_* bits above (sw_run_noalloc:
+                           SW_FLAG_GENERIC, SW_FLAG_LENGTHENED, SW_FLAG_FLATTENED only;
+                           batches: 0, SW_FLAG_LENGTHENED or SW_FLAG_FLATTENED) */
 } sw_problem;
 
 typedef struct sw_handle sw_handle;
@@ -180,8 +190,10 @@ SW_API int sw_hybrid_split(int64_t tiles, int32_t work_factor, int32_t cpu_threa
  * mirrors (2 x the flank scratch + one state, pinned) and starts the threads; both
  * are kept by the handle until sw_destroy (a call with another thread count restarts
  * the threads). Not safe to call concurrently on one handle.
- * Errors: SW_ERR_BAD_ARG (method not swept, the split above, NULL state, nsteps < 0),
- * SW_ERR_OOM, SW_ERR_CUDA. */
+ * The host threads implement the lengthened Euler form only: an Euler handle must
+ * run lengthened (SW_FLAG_LENGTHENED, or a width that rules out the flattened form).
+ * Errors: SW_ERR_BAD_ARG (method not swept, a flattened Euler handle, the split
+ * above, NULL state, nsteps < 0), SW_ERR_OOM, SW_ERR_CUDA. */
 SW_API int sw_run_hybrid(sw_handle *h, void *state, int64_t nsteps, int32_t work_factor, int32_t cpu_threads,
                          void *stream);
 
@@ -236,29 +248,38 @@ SW_API int32_t sw_tile_width(const sw_handle *h);
  * inside a framework whose memory pool owns the device (a direct cudaMalloc
  * fails or escapes the pool's accounting) and latency-critical loops that
  * allow no allocation after start-up (cudaMalloc/cudaFree may synchronise).
- * It runs the same swept phases as sw_run (method must be SW_SWEPT), but the
+ * It runs the same swept phases as sw_run (method must be SW_SWEPT; same default
+ * width and Euler form; always the generic phase kernel, same bits), but the
  * flank buffers live in one static device array of SW_NOALLOC_SCRATCH_BYTES
  * (16 MiB) compiled into the library, which every GPU that loads the library
  * holds until the process exits. The caller passes the state, as for sw_run.
  * Scratch needed: 2 * round_up_256(K * (n/W + 1) * 2W * element_size) bytes,
- * K = 1 (heat FP64/FP32), 2 (heat FP32_COMP), 7 (Euler FP64/FP32),
- * 10 (Euler FP32_COMP); larger problems are rejected with SW_ERR_TOO_LARGE
- * before any launch (e.g. heat FP64 at W = 1024 fits n up to ~512k cells).
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. All calls share the array and it keeps the last
- * call's contents (nothing in it needs to start at zero); calls that overlap
- * on the GPU race on it and must be serialised by the caller.
- * Errors: SW_ERR_BAD_ARG (as sw_create, or method != SW_SWEPT),
- * SW_ERR_TOO_LARGE, SW_ERR_UNSUPPORTED, SW_ERR_CUDA. */
+ * K = 1 (heat FP64/FP32), 2 (heat FP32_COMP), 7 (Euler FP64/FP32 lengthened),
+ * 6 (flattened), 10 (Euler FP32_COMP lengthened), 9 (flattened); larger problems
+ * are rejected with SW_ERR_TOO_LARGE before any launch (e.g. heat FP64 at
+ * W = 1024 fits n up to ~512k cells).
+ * Every call looks up the array's device address (cudaGetSymbolAddress, a
+ * host-side lookup that allocates nothing) with the caller's device current, so
+ * a device reset cannot leave a stale address. The first call on a device also
+ * loads the library's device code there; make that first call before any
+ * stream capture. All calls share the array and it keeps the last call's
+ * contents (nothing in it needs to start at zero); calls that overlap on the
+ * GPU race on it and must be serialised by the caller. A CUDA error already
+ * pending on the calling thread is reported as SW_ERR_CUDA without launching
+ * (and is left pending); launches stop at the first that fails.
+ * Returns SW_WARN_UNSTABLE after a successful heat run with r > 1/2, as sw_create.
+ * Errors: SW_ERR_BAD_ARG (the rules of sw_create, method != SW_SWEPT, other
+ * flags), SW_ERR_TOO_LARGE, SW_ERR_UNSUPPORTED, SW_ERR_CUDA. */
 SW_API int sw_run_noalloc(const sw_problem *p, void *state, int64_t nsteps, void *stream);
 
 /* ---- batches: many independent problems in one persistent launch ------------
  * (Section 6 of the paper tunes the block size per problem; the batched launch
  * and its device-side work queue are this library's addition.)
  * sw_batch_create: `count` problems (all of one precision, method SW_SWEPT,
- * flags 0 or, for an Euler problem, SW_FLAG_FLATTENED (then W % 4 == 0 and
- * W >= 8), each with an explicit tile_width), problem i's device state at
+ * the field rules of sw_create, each with an explicit tile_width; flags 0 or, for
+ * an Euler problem, SW_FLAG_LENGTHENED or SW_FLAG_FLATTENED (then W % 4 == 0 and
+ * W >= 8); each Euler problem runs in the form sw_run would take for it), problem
+ * i's device state at
  * states[i] (layout as for sw_run, owned by the caller and used by every run),
  * each advanced `nsteps` time steps per sw_batch_run. Allocates the flank
  * buffers, per-structure completion flags and the work tables (owned by the
@@ -293,8 +314,10 @@ SW_API void sw_batch_destroy(sw_batch *b);
  * few short runs): times `probe_steps` steps of a uniform state
  * of the problem for each W in {32, ..., 1024} that divides n (with n >= 2W),
  * using the problem's own flags (SW_FLAG_GENERIC tunes the generic kernel that
- * batches use), and writes the fastest to inout->tile_width. Allocates a
- * temporary state; synchronises `stream`. */
+ * batches use), and writes the fastest to inout->tile_width. For an Euler
+ * problem with neither SW_FLAG_LENGTHENED nor SW_FLAG_FLATTENED it times both
+ * forms of Section 4.3 at each W and ORs the faster form's flag into
+ * inout->flags. Allocates a temporary state; synchronises `stream`. */
 SW_API int sw_autotune(sw_problem *inout, int64_t probe_steps, void *stream);
 
 SW_API const char *sw_status_string(int status);

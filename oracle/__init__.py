@@ -52,6 +52,8 @@ def _load():
         pd = ctypes.POINTER(ctypes.c_double)
         pl = ctypes.POINTER(ctypes.c_int64)
         lib.orc_num_threads.restype = i32
+        lib.orc_set_threads.argtypes = [i32]
+        lib.orc_set_threads.restype = None
         lib.orc_heat_run.argtypes = [i64, f64, i32, i64, pd]
         lib.orc_heat_run.restype = i32
         lib.orc_heat_modes.argtypes = [i64, f64, i64, i32, pd, pl, pl, i64, pd]
@@ -79,6 +81,11 @@ def _lptr(a: np.ndarray):
 def num_threads() -> int:
     """Threads the oracle's parallel cell loops use (OpenMP)."""
     return int(_load().orc_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Use `n` threads in the parallel cell loops from now on (results are unchanged)."""
+    _load().orc_set_threads(int(n))
 
 
 def heat_run(u0, r: float, nsteps: int, boundary: int = PERIODIC) -> np.ndarray:

@@ -52,6 +52,17 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads of the parallel cell loops from here on (timing of the 1-core rate;
+ * small grids). Results do not depend on it: every cell is computed alone. */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Heat equation, FTCS (Section 4.2: first-order forward in time, central in
  * space). Reading: u_j <- u_j + r*((u_{j-1} + u_{j+1}) - 2 u_j), r = alpha dt/dx^2,

@@ -57,8 +57,8 @@ def tune_widths(items, precision=S.SW_FP32_COMP, candidates=(256, 512, 1024), sa
     does, so queue and occupancy effects are part of what is timed (a few small
     probe problems would leave most SMs idle and favour narrow tiles). Each timed
     run covers two phases of the widest candidate, after one untimed run of the
-    same length. Returns {scheme: (width cap, flags)}: flags 0, or for Euler
-    SW_FLAG_FLATTENED when the flattened form (Section 4.3) times faster."""
+    same length. Returns {scheme: (width cap, flags)}: flags 0 for heat; for Euler
+    SW_FLAG_LENGTHENED or SW_FLAG_FLATTENED, the form (Section 4.3) that timed faster."""
     import torch
     widths = {}
     for scheme in sorted({it.scheme for it in items}):
@@ -70,7 +70,7 @@ def tune_widths(items, precision=S.SW_FP32_COMP, candidates=(256, 512, 1024), sa
         levels = max(candidates)
         steps = levels if scheme == "heat" else levels // 4
         best = None
-        forms = (0, S.SW_FLAG_FLATTENED) if scheme == "euler" else (0,)
+        forms = (S.SW_FLAG_LENGTHENED, S.SW_FLAG_FLATTENED) if scheme == "euler" else (0,)
         for cap, flags in [(c, f) for c in candidates for f in forms]:
             probs = [_problem(it, precision, fit_width(it.n, cap, flags), flags) for it in sample]
             states = [S.to_state(p, torch.as_tensor(it.planes.reshape(-1), device="cuda"))

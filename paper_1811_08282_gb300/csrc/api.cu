@@ -20,6 +20,7 @@
 
 #include "../../include/swept.h"
 #include "cpu_phase.h"
+#include "problem.h"
 #include "fold.h"
 #include "perstep.cuh"
 #include "schemes.cuh"
@@ -141,43 +142,8 @@ int planes_of(const sw_problem &p) {
 
 size_t elem_size(const sw_problem &p) { return p.precision == SW_FP64 ? sizeof(double) : sizeof(float); }
 
-bool flattened(const sw_problem &p) { return p.scheme == SW_EULER && (p.flags & SW_FLAG_FLATTENED); }
-
-int validate(const sw_problem *p) {
-    if (!p) return SW_ERR_BAD_ARG;
-    if (p->scheme != SW_HEAT && p->scheme != SW_EULER) return SW_ERR_BAD_ARG;
-    if (p->precision < SW_FP64 || p->precision > SW_FP32_COMP) return SW_ERR_BAD_ARG;
-    if (p->boundary != SW_PERIODIC && p->boundary != SW_TRANSMISSIVE) return SW_ERR_BAD_ARG;
-    if (p->method != SW_SWEPT && p->method != SW_PERSTEP) return SW_ERR_BAD_ARG;
-    if (p->flags & ~(SW_FLAG_GENERIC | SW_FLAG_EULER_FOLD | SW_FLAG_LENGTHENED | SW_FLAG_FLATTENED | SW_FLAG_GRAPH))
-        return SW_ERR_BAD_ARG;
-    if (p->n < 4 || p->n > (int64_t(1) << 40)) return SW_ERR_BAD_ARG;
-    if (p->scheme == SW_HEAT) {
-        if (!(p->r > 0.0) || !(p->r < 1e6)) return SW_ERR_BAD_ARG;
-    } else {
-        if (!(p->dt_dx > 0.0) || !(p->gamma > 1.0) || !(p->gamma < 1e6)) return SW_ERR_BAD_ARG;
-    }
-    if (p->method == SW_SWEPT) {
-        const int W = p->tile_width == 0 ? 0 : p->tile_width;
-        if (W != 0) {
-            if (W < SW_MIN_TILE || W > SW_MAX_TILE || (W & 1)) return SW_ERR_BAD_ARG;
-            if (p->n % W != 0 || p->n < 2 * (int64_t)W) return SW_ERR_BAD_ARG;
-            // flattened Euler: radius-2 windows, W/4 levels per phase half
-            if (flattened(*p) && (W % 4 != 0 || W < 8)) return SW_ERR_BAD_ARG;
-        }
-    } else if (p->tile_width != 0 && (p->tile_width < 0)) {
-        return SW_ERR_BAD_ARG;
-    }
-    return SW_OK;
-}
-
-// Default base width: the largest of 1024, 512, ..., 4 that divides n with at
-// least two tiles (Section 6 recommends large blocks, 768-1024).
-int default_width(const sw_problem &p) {
-    for (int W = SW_MAX_TILE; W >= (flattened(p) ? 8 : SW_MIN_TILE); W >>= 1)
-        if (p.n % W == 0 && p.n >= 2 * (int64_t)W) return W;
-    return 0;
-}
+// the form a handle runs in (Section 4.3): fixed at sw_create from the problem and its W
+bool flattened(const sw_problem &p) { return euler_flattened(p, p.tile_width); }
 
 int swept_threads(int W) {
     int t = W / 2;
@@ -476,7 +442,7 @@ int launch_perstep_euler_t(sw_handle *h, void *state, int64_t nsteps, cudaStream
     const unsigned grid = (unsigned)((n + B - 1) / B);
     T *q = reinterpret_cast<T *>(state);
     T *s = reinterpret_cast<T *>(h->scratch);
-    if (h->prob.flags & SW_FLAG_LENGTHENED) {
+    if (!flattened(h->prob)) {
         // lengthened form: four 3-point sub-step launches per step
         const size_t smem4 = (size_t(4) * (B + 2) + size_t(3) * (B + 1)) * sizeof(T);
         for (int64_t k = 0; k < nsteps; ++k) {
@@ -597,6 +563,40 @@ __global__ void k_check_physical(const void *st, int64_t n, int prec, double gam
 
 }  // namespace
 
+namespace sw {
+
+int validate_problem(const sw_problem *p) {
+    if (!p) return SW_ERR_BAD_ARG;
+    if (p->scheme != SW_HEAT && p->scheme != SW_EULER) return SW_ERR_BAD_ARG;
+    if (p->precision < SW_FP64 || p->precision > SW_FP32_COMP) return SW_ERR_BAD_ARG;
+    if (p->boundary != SW_PERIODIC && p->boundary != SW_TRANSMISSIVE) return SW_ERR_BAD_ARG;
+    if (p->method != SW_SWEPT && p->method != SW_PERSTEP) return SW_ERR_BAD_ARG;
+    if (p->flags & ~(SW_FLAG_GENERIC | SW_FLAG_EULER_FOLD | SW_FLAG_LENGTHENED | SW_FLAG_FLATTENED | SW_FLAG_GRAPH))
+        return SW_ERR_BAD_ARG;
+    if ((p->flags & SW_FLAG_LENGTHENED) && (p->flags & SW_FLAG_FLATTENED)) return SW_ERR_BAD_ARG;
+    if (p->n < 4 || p->n > (int64_t(1) << 40)) return SW_ERR_BAD_ARG;
+    if (p->scheme == SW_HEAT) {
+        if (!(p->r > 0.0) || !(p->r < 1e6)) return SW_ERR_BAD_ARG;
+    } else {
+        if (!(p->dt_dx > 0.0) || !(p->gamma > 1.0) || !(p->gamma < 1e6)) return SW_ERR_BAD_ARG;
+    }
+    if (p->method == SW_SWEPT) {
+        const int W = p->tile_width;
+        if (W != 0) {
+            if (W < SW_MIN_TILE || W > SW_MAX_TILE || (W & 1)) return SW_ERR_BAD_ARG;
+            if (p->n % W != 0 || p->n < 2 * (int64_t)W) return SW_ERR_BAD_ARG;
+            // an explicitly flattened Euler problem: radius-2 windows, W/4 levels per phase half
+            if (p->scheme == SW_EULER && (p->flags & SW_FLAG_FLATTENED) && (W % 4 != 0 || W < 8))
+                return SW_ERR_BAD_ARG;
+        }
+    } else if (p->tile_width < 0) {
+        return SW_ERR_BAD_ARG;
+    }
+    return SW_OK;
+}
+
+}  // namespace sw
+
 // ===================================================================== C ABI
 extern "C" {
 
@@ -621,18 +621,18 @@ const char *sw_status_string(int s) {
 }
 
 int sw_state_planes(const sw_problem *p) {
-    if (validate(p) != SW_OK) return SW_ERR_BAD_ARG;
+    if (validate_problem(p) != SW_OK) return SW_ERR_BAD_ARG;
     return planes_of(*p);
 }
 
 int64_t sw_state_bytes(const sw_problem *p) {
-    if (validate(p) != SW_OK) return SW_ERR_BAD_ARG;
+    if (validate_problem(p) != SW_OK) return SW_ERR_BAD_ARG;
     return int64_t(planes_of(*p)) * p->n * int64_t(elem_size(*p));
 }
 
 int sw_create(const sw_problem *p, sw_handle **out) {
     if (!out) return SW_ERR_BAD_ARG;
-    int rc = validate(p);
+    int rc = validate_problem(p);
     if (rc != SW_OK) return rc;
     sw_handle *h = new (std::nothrow) sw_handle();
     if (!h) return SW_ERR_OOM;
@@ -661,8 +661,9 @@ int sw_create(const sw_problem *p, sw_handle **out) {
     };
     cudaError_t e;
     if (p->method == SW_SWEPT) {
-        h->W = p->tile_width ? p->tile_width : default_width(*p);
+        h->W = p->tile_width ? p->tile_width : default_tile_width(*p);
         if (h->W == 0) return fail(SW_ERR_BAD_ARG);
+        h->prob.tile_width = h->W;  // the form (Section 4.3) follows the width in use
         h->H = h->W / 2;
         h->M = p->n / h->W;
         h->S = h->M + 1;
@@ -677,7 +678,7 @@ int sw_create(const sw_problem *p, sw_handle **out) {
             default: h->nsnap = HeatPolicy<2>::NSNAP; h->smem = swept_smem<HeatPolicy<2>>(h->W);
                 prc = prepare_swept_kernel<HeatPolicy<2>>(h->smem); break;
             }
-        } else if (flattened(*p)) {
+        } else if (flattened(h->prob)) {
             switch (p->precision) {
             case SW_FP64: h->nsnap = EulerFlatPolicy<0>::NSNAP; h->smem = swept_smem<EulerFlatPolicy<0>>(h->W);
                 prc = prepare_swept_kernel<EulerFlatPolicy<0>>(h->smem); break;
@@ -939,7 +940,7 @@ int sw_run_host(sw_handle *h, const void *state_in, void *state_out, int64_t nst
 }
 
 int sw_pack_fp64(const sw_problem *p, const double *src, void *dst, void *stream) {
-    if (validate(p) != SW_OK || !src || !dst) return SW_ERR_BAD_ARG;
+    if (validate_problem(p) != SW_OK || !src || !dst) return SW_ERR_BAD_ARG;
     const int64_t count = int64_t(scheme_nv(*p)) * p->n;
     k_pack<<<grid_for(count, 256, 152 * 8), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(src, dst, count,
                                                                                                p->precision);
@@ -947,7 +948,7 @@ int sw_pack_fp64(const sw_problem *p, const double *src, void *dst, void *stream
 }
 
 int sw_unpack_fp64(const sw_problem *p, const void *src, double *dst, void *stream) {
-    if (validate(p) != SW_OK || !src || !dst) return SW_ERR_BAD_ARG;
+    if (validate_problem(p) != SW_OK || !src || !dst) return SW_ERR_BAD_ARG;
     const int64_t count = int64_t(scheme_nv(*p)) * p->n;
     k_unpack<<<grid_for(count, 256, 152 * 8), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(src, dst, count,
                                                                                                  p->precision);

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/swept.h"
+#include "problem.h"
 #include "schemes.cuh"
 #include "swept_phase.cuh"
 
@@ -274,17 +275,10 @@ int sw_batch_create(const sw_problem *probs, void *const *states, int32_t count,
     for (int32_t i = 0; i < count; ++i) {
         const sw_problem &p = probs[i];
         if (!states[i] || p.precision != prec || p.method != SW_SWEPT) return SW_ERR_BAD_ARG;
-        // flags: 0, or the flattened form for an Euler problem (radius-2 windows: W % 4 == 0, W >= 8)
-        const bool flat = p.flags == SW_FLAG_FLATTENED && p.scheme == SW_EULER;
-        if (p.flags != 0 && !flat) return SW_ERR_BAD_ARG;
-        if (flat && (p.tile_width % 4 != 0 || p.tile_width < 8)) return SW_ERR_BAD_ARG;
-        if (p.scheme != SW_HEAT && p.scheme != SW_EULER) return SW_ERR_BAD_ARG;
-        if (p.boundary != SW_PERIODIC && p.boundary != SW_TRANSMISSIVE) return SW_ERR_BAD_ARG;
-        if (prec < SW_FP64 || prec > SW_FP32_COMP) return SW_ERR_BAD_ARG;
-        const int W = p.tile_width;
-        if (W < SW_MIN_TILE || W > SW_MAX_TILE || (W & 1) || p.n < 2 * (int64_t)W || p.n % W) return SW_ERR_BAD_ARG;
-        if (p.scheme == SW_HEAT ? !(p.r > 0.0 && p.r < 1e6) : !(p.dt_dx > 0.0 && p.gamma > 1.0 && p.gamma < 1e6))
-            return SW_ERR_BAD_ARG;
+        // the rules of sw_create, an explicit width, and flags 0 or an Euler form (Section 4.3)
+        if (validate_problem(&p) != SW_OK || p.tile_width == 0) return SW_ERR_BAD_ARG;
+        if (p.flags & ~(SW_FLAG_LENGTHENED | SW_FLAG_FLATTENED)) return SW_ERR_BAD_ARG;
+        if (p.scheme != SW_EULER && p.flags != 0) return SW_ERR_BAD_ARG;
     }
     sw_batch *b = new (std::nothrow) sw_batch();
     if (!b) return SW_ERR_OOM;
@@ -306,7 +300,7 @@ int sw_batch_create(const sw_problem *probs, void *const *states, int32_t count,
         d.scheme = p.scheme;
         d.periodic = p.boundary == SW_PERIODIC;
         d.W = p.tile_width;
-        d.flat = (p.scheme == SW_EULER && p.flags == SW_FLAG_FLATTENED) ? 1 : 0;
+        d.flat = euler_flattened(p, p.tile_width) ? 1 : 0;  // the form sw_run would take
         d.n = p.n;
         d.M = p.n / p.tile_width;
         d.S = d.M + 1;
@@ -521,25 +515,31 @@ int sw_autotune(sw_problem *inout, int64_t probe_steps, void *stream) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best_w = 0;
+    int best_w = 0, best_form = 0;
     float best_t = 0.f;
+    // Euler without an explicit form: both data-structure forms of Section 4.3 are timed
+    const bool both_forms = p.scheme == SW_EULER && !(p.flags & (SW_FLAG_LENGTHENED | SW_FLAG_FLATTENED));
     for (int W = SW_MIN_TILE; W <= SW_MAX_TILE; W *= 2) {
         if (W < 32 || p.n % W || p.n < 2 * (int64_t)W) continue;
-        sw_problem q = p;
-        q.tile_width = W;
-        sw_handle *h = nullptr;
-        if (sw_create(&q, &h) < 0) continue;
-        sw_run(h, state, probe_steps, stream);  // warm-up
-        cudaEventRecord(e0, st);
-        sw_run(h, state, probe_steps, stream);
-        cudaEventRecord(e1, st);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        sw_destroy(h);
-        if (best_w == 0 || ms < best_t) {
-            best_w = W;
-            best_t = ms;
+        for (int k = 0; k < (both_forms ? 2 : 1); ++k) {
+            sw_problem q = p;
+            q.tile_width = W;
+            if (both_forms) q.flags |= (k == 0 ? SW_FLAG_LENGTHENED : SW_FLAG_FLATTENED);
+            sw_handle *h = nullptr;
+            if (sw_create(&q, &h) < 0) continue;
+            sw_run(h, state, probe_steps, stream);  // warm-up
+            cudaEventRecord(e0, st);
+            sw_run(h, state, probe_steps, stream);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            sw_destroy(h);
+            if (best_w == 0 || ms < best_t) {
+                best_w = W;
+                best_t = ms;
+                best_form = both_forms ? (k == 0 ? SW_FLAG_LENGTHENED : SW_FLAG_FLATTENED) : 0;
+            }
         }
     }
     cudaEventDestroy(e0);
@@ -547,6 +547,7 @@ int sw_autotune(sw_problem *inout, int64_t probe_steps, void *stream) {
     cudaFree(state);
     if (best_w == 0) return SW_ERR_UNSUPPORTED;
     inout->tile_width = best_w;
+    inout->flags |= best_form;
     return SW_OK;
 }
 

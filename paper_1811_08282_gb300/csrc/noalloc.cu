@@ -13,14 +13,15 @@
 // contents. Nothing in it has to start at zero: each phase writes the flanks
 // it hands on before the next phase reads them. Calls that overlap on the GPU
 // (different streams, or different host threads) race on the array and give
-// wrong results; serialise them.
+// wrong results; serialise them. The problem is validated by the same rules as
+// sw_create and runs in the same data-structure form as sw_run would choose.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <mutex>
 #include <type_traits>
 
 #include "../../include/swept.h"
+#include "problem.h"
 #include "schemes.cuh"
 #include "swept_phase.cuh"
 
@@ -30,36 +31,38 @@ namespace {
 
 static __device__ __align__(256) unsigned char sw_noalloc_scratch[SW_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-void *g_scratch_addr[kMaxDevices] = {};
-
 // Host code may not use &sw_noalloc_scratch as a device address (it names a
-// host-side stand-in). Look the real address up once per device, with that
-// device current, and cache it.
+// host-side stand-in). The real address is looked up with the caller's device
+// current on every call: a host-side lookup that allocates nothing, so a device
+// reset or a new primary context, after which the module is loaded again and
+// the array may sit elsewhere, never leaves a stale address behind. The first
+// lookup on a device also loads the library's device code there.
 int scratch_address(void **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return SW_ERR_CUDA;
-    if (dev < 0 || dev >= kMaxDevices) return SW_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, sw_noalloc_scratch);
-        if (e != cudaSuccess || !p) return SW_ERR_CUDA;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, sw_noalloc_scratch);
+    if (e != cudaSuccess || !p) return SW_ERR_CUDA;
+    *out = p;
     return SW_OK;
+}
+
+// Bytes of one flank buffer, rounded up to 256, or 0 when two of them would not
+// fit in the static array. The structure count is compared against the bound
+// before any product is formed, so no size can wrap.
+template <class P> size_t flank_buffer_bytes(int64_t S, int W) {
+    const size_t per_struct = size_t(P::NSNAP) * 2 * size_t(W) * sizeof(typename P::T);
+    if (S <= 0 || size_t(S) > SW_NOALLOC_SCRATCH_BYTES / (2 * per_struct)) return 0;
+    const size_t bytes = (size_t(S) * per_struct + 255) / 256 * 256;
+    return 2 * bytes <= SW_NOALLOC_SCRATCH_BYTES ? bytes : 0;
 }
 
 template <class P>
 int run_phases(const sw_problem &prob, int W, void *scratch, void *state, int64_t L, cudaStream_t st) {
     using T = typename P::T;
-    const int H = W / 2;
+    constexpr int R = P::R;
+    const int H = W / 2, HL = H / R;  // levels per phase half (radius-2 windows: W/4)
     const int64_t M = prob.n / W, S = M + 1;
-    const size_t buf_elems = size_t(P::NSNAP) * size_t(S) * 2 * W;
-    const size_t buf_bytes = (buf_elems * sizeof(T) + 255) / 256 * 256;
-    if (2 * buf_bytes > SW_NOALLOC_SCRATCH_BYTES) return SW_ERR_TOO_LARGE;
+    const size_t buf_bytes = flank_buffer_bytes<P>(S, W);
+    if (buf_bytes == 0) return SW_ERR_TOO_LARGE;
     T *flank[2] = {reinterpret_cast<T *>(scratch),
                    reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(scratch) + buf_bytes)};
     const size_t smem = swept_smem_elems<P>(W) * sizeof(T);
@@ -68,7 +71,7 @@ int run_phases(const sw_problem &prob, int W, void *scratch, void *state, int64_
         cudaFuncSetAttribute(k_swept_phase<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
         return SW_ERR_CUDA;
-    int threads = std::min(512, std::max(32, (W / 2 + 31) / 32 * 32));
+    const int threads = std::min(512, std::max(32, (W / 2 + 31) / 32 * 32));
     typename P::Params prm{};
     if constexpr (std::is_same<typename P::Params, HeatParams>::value) {
         prm.r = prob.r;
@@ -85,7 +88,7 @@ int run_phases(const sw_problem &prob, int W, void *scratch, void *state, int64_
         prm.hlamf = (float)(0.5 * prob.dt_dx);
     }
     const bool periodic = prob.boundary == SW_PERIODIC;
-    const int64_t P_last = (L + H - 1) / H;
+    const int64_t P_last = (L + HL - 1) / HL;
     for (int64_t p = 0; p <= P_last; ++p) {
         PhaseArgs<T> a{};
         a.n = prob.n;
@@ -93,11 +96,11 @@ int run_phases(const sw_problem &prob, int W, void *scratch, void *state, int64_
         a.H = H;
         a.periodic = periodic ? 1 : 0;
         a.p = (p == 0) ? 0 : (int)(2 - (p & 1));
-        a.F = p * H;
-        a.lower = (p == 0) ? 0 : (int)std::min<int64_t>(H, L - (p - 1) * H);
-        a.upper = (p == P_last) ? 0 : (int)std::min<int64_t>(H - 1, L - p * H);
+        a.F = p * HL;
+        a.lower = (p == 0) ? 0 : (int)std::min<int64_t>(HL, L - (p - 1) * HL);
+        a.upper = (p == P_last) ? 0 : (int)std::min<int64_t>(HL - 1, L - p * HL);
         a.write_lower = (p == P_last) ? 1 : 0;
-        a.write_upper = (a.upper > 0 && p * H + a.upper == L) ? 1 : 0;
+        a.write_upper = (a.upper > 0 && p * HL + a.upper == L) ? 1 : 0;
         a.tiles = M;
         a.nstruct = (p & 1) ? (periodic ? M : M + 1) : M;
         a.nstruct_max = S;
@@ -105,45 +108,51 @@ int run_phases(const sw_problem &prob, int W, void *scratch, void *state, int64_
         a.flank_out = flank[p & 1];
         a.state = reinterpret_cast<T *>(state);
         k_swept_phase<P><<<(unsigned)a.nstruct, threads, smem, st>>>(a, prm);
+        // stop at the first launch that fails (nothing else is pending: checked on entry)
+        if (cudaGetLastError() != cudaSuccess) return SW_ERR_CUDA;
     }
-    return cudaGetLastError() == cudaSuccess ? SW_OK : SW_ERR_CUDA;
+    return SW_OK;
 }
 
 }  // namespace
 
 extern "C" int sw_run_noalloc(const sw_problem *p, void *state, int64_t nsteps, void *stream) {
     if (!p || !state || nsteps < 0) return SW_ERR_BAD_ARG;
-    if (p->method != SW_SWEPT || p->flags != 0) return SW_ERR_BAD_ARG;
-    if (p->scheme != SW_HEAT && p->scheme != SW_EULER) return SW_ERR_BAD_ARG;
-    if (p->precision < SW_FP64 || p->precision > SW_FP32_COMP) return SW_ERR_BAD_ARG;
-    if (p->boundary != SW_PERIODIC && p->boundary != SW_TRANSMISSIVE) return SW_ERR_BAD_ARG;
-    if (p->scheme == SW_HEAT ? !(p->r > 0.0 && p->r < 1e6)
-                             : !(p->dt_dx > 0.0 && p->gamma > 1.0 && p->gamma < 1e6))
+    if (validate_problem(p) != SW_OK) return SW_ERR_BAD_ARG;
+    // the generic phase kernel and the two data-structure forms only
+    if (p->method != SW_SWEPT || (p->flags & ~(SW_FLAG_GENERIC | SW_FLAG_LENGTHENED | SW_FLAG_FLATTENED)))
         return SW_ERR_BAD_ARG;
-    int W = p->tile_width;
-    if (W == 0) {
-        for (W = SW_MAX_TILE; W >= SW_MIN_TILE; W >>= 1)
-            if (p->n % W == 0 && p->n >= 2 * (int64_t)W) break;
-        if (W < SW_MIN_TILE) return SW_ERR_BAD_ARG;
-    }
-    if (W < SW_MIN_TILE || W > SW_MAX_TILE || (W & 1) || p->n < 2 * (int64_t)W || p->n % W != 0)
-        return SW_ERR_BAD_ARG;
-    if (nsteps == 0) return SW_OK;
+    const int W = p->tile_width ? p->tile_width : default_tile_width(*p);
+    if (W == 0) return SW_ERR_BAD_ARG;
+    const bool flat = euler_flattened(*p, W);
+    const int warn = (p->scheme == SW_HEAT && p->r > 0.5) ? SW_WARN_UNSTABLE : SW_OK;
+    if (nsteps == 0) return warn;
+    // a CUDA error already pending on this thread belongs to earlier work: report it
+    // without launching (and without clearing it) rather than mistake it for ours
+    if (cudaPeekAtLastError() != cudaSuccess) return SW_ERR_CUDA;
     void *scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc != SW_OK) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int64_t L = nsteps * (p->scheme == SW_HEAT ? 1 : 4);
+    const int64_t L = nsteps * (p->scheme == SW_HEAT ? 1 : (flat ? 2 : 4));
     if (p->scheme == SW_HEAT) {
         switch (p->precision) {
-        case SW_FP64: return run_phases<HeatPolicy<0>>(*p, W, scratch, state, L, st);
-        case SW_FP32: return run_phases<HeatPolicy<1>>(*p, W, scratch, state, L, st);
-        default: return run_phases<HeatPolicy<2>>(*p, W, scratch, state, L, st);
+        case SW_FP64: rc = run_phases<HeatPolicy<0>>(*p, W, scratch, state, L, st); break;
+        case SW_FP32: rc = run_phases<HeatPolicy<1>>(*p, W, scratch, state, L, st); break;
+        default: rc = run_phases<HeatPolicy<2>>(*p, W, scratch, state, L, st); break;
+        }
+    } else if (flat) {
+        switch (p->precision) {
+        case SW_FP64: rc = run_phases<EulerFlatPolicy<0>>(*p, W, scratch, state, L, st); break;
+        case SW_FP32: rc = run_phases<EulerFlatPolicy<1>>(*p, W, scratch, state, L, st); break;
+        default: rc = run_phases<EulerFlatPolicyComp>(*p, W, scratch, state, L, st); break;
+        }
+    } else {
+        switch (p->precision) {
+        case SW_FP64: rc = run_phases<EulerPolicy<0>>(*p, W, scratch, state, L, st); break;
+        case SW_FP32: rc = run_phases<EulerPolicy<1>>(*p, W, scratch, state, L, st); break;
+        default: rc = run_phases<EulerPolicyComp>(*p, W, scratch, state, L, st); break;
         }
     }
-    switch (p->precision) {
-    case SW_FP64: return run_phases<EulerPolicy<0>>(*p, W, scratch, state, L, st);
-    case SW_FP32: return run_phases<EulerPolicy<1>>(*p, W, scratch, state, L, st);
-    default: return run_phases<EulerPolicyComp>(*p, W, scratch, state, L, st);
-    }
+    return rc != SW_OK ? rc : warn;
 }

@@ -159,22 +159,32 @@ class BatchItem:
     planes: np.ndarray  # FP64 initial state, shape (nv, n)
 
 
+def batch_lengths(count: int, seed: int, lo_exp: float = 10.0, hi_exp: float = 18.0,
+                  multiple: int = 256) -> np.ndarray:
+    """Problem lengths of a batch: log-uniform in [2^lo_exp, 2^hi_exp], rounded to a
+    multiple of `multiple` (at least `multiple`)."""
+    e = uniform(seed, count, lo_exp, hi_exp, stream=21)
+    return np.maximum(multiple, np.round(2.0 ** e / multiple).astype(np.int64) * multiple)
+
+
+def batch_item(i: int, n: int, r: float, seed: int) -> BatchItem:
+    """Problem i of a batch of length n: even i heat (r, 8 sine modes, k <= min(64, n/8)),
+    odd i Euler (one Riemann problem, interface at the middle, states as in
+    riemann_segments)."""
+    if i % 2 == 0:
+        modes = heat_modes(n, 8, seed=seed * 100003 + i, kmax=min(64, max(1, n // 8)))
+        return BatchItem("heat", n, float(r), heat_initial(modes)[None])
+    seg = riemann_segments(n, 2, seed * 100003 + i)
+    return BatchItem("euler", n, 0.0, riemann_initial(seg))
+
+
 def batch_problems(count: int, seed: int, lo_exp: float = 10.0, hi_exp: float = 18.0,
-                   multiple: int = 256):
+                   multiple: int = 256, indices=None):
     """Lengths log-uniform in [2^lo_exp, 2^hi_exp] rounded to a multiple of `multiple`;
     even indices heat (r ~ U[0.1, 0.45], 8 sine modes, k <= min(64, n/8)), odd indices
     Euler (one Riemann problem per domain, interface at the middle, states as in
-    riemann_segments)."""
-    e = uniform(seed, count, lo_exp, hi_exp, stream=21)
-    ns = np.maximum(multiple, np.round(2.0 ** e / multiple).astype(np.int64) * multiple)
+    riemann_segments). `indices`: only those problems of the batch (same draws)."""
+    ns = batch_lengths(count, seed, lo_exp, hi_exp, multiple)
     rs = uniform(seed, count, 0.1, 0.45, stream=22)
-    out = []
-    for i in range(count):
-        n = int(ns[i])
-        if i % 2 == 0:
-            modes = heat_modes(n, 8, seed=seed * 100003 + i, kmax=min(64, max(1, n // 8)))
-            out.append(BatchItem("heat", n, float(rs[i]), heat_initial(modes)[None]))
-        else:
-            seg = riemann_segments(n, 2, seed * 100003 + i)
-            out.append(BatchItem("euler", n, 0.0, riemann_initial(seg)))
-    return out
+    which = range(count) if indices is None else indices
+    return [batch_item(i, int(ns[i]), float(rs[i]), seed) for i in which]

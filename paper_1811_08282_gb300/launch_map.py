@@ -154,7 +154,7 @@ def run_map(scheme: str, precision: int, exps, widths, target: float, cap: int, 
 
 def run_forms(precision: int, exps, widths, target: float, cap: int, reps: int, emit=print):
     """Section 4.3 / Fig. 3 on this GPU: µs per step of the four Euler forms per N."""
-    forms = {"swept_lengthened": (S.SW_SWEPT, 0), "swept_flattened": (S.SW_SWEPT, S.SW_FLAG_FLATTENED),
+    forms = {"swept_lengthened": (S.SW_SWEPT, S.SW_FLAG_LENGTHENED), "swept_flattened": (S.SW_SWEPT, S.SW_FLAG_FLATTENED),
              "perstep_flattened": (S.SW_PERSTEP, 0), "perstep_lengthened": (S.SW_PERSTEP, S.SW_FLAG_LENGTHENED)}
     for e in exps:
         n = 1 << e

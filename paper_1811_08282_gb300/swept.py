@@ -15,7 +15,7 @@ from dataclasses import dataclass
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libswept.so")
 
-ABI_VERSION = 2  # SW_ABI_VERSION of include/swept.h
+ABI_VERSION = 3  # SW_ABI_VERSION of include/swept.h
 SW_HEAT, SW_EULER = 0, 1
 SW_FP64, SW_FP32, SW_FP32_COMP = 0, 1, 2
 SW_PERIODIC, SW_TRANSMISSIVE = 0, 1
@@ -198,13 +198,13 @@ def sw_unpack_fp64(p: Problem, src_state, dst_fp64, stream=None) -> None:
            "sw_unpack_fp64")
 
 
-def sw_run_noalloc(p: Problem, state, nsteps: int, stream=None) -> None:
+def sw_run_noalloc(p: Problem, state, nsteps: int, stream=None) -> int:
     """Swept run with no device allocation (flank scratch in the library's static
     16 MiB device array); for callers that cannot call cudaMalloc. Calls share the
-    array: do not overlap them on the GPU."""
+    array: do not overlap them on the GPU. Returns SW_OK or SW_WARN_UNSTABLE."""
     cp = p.c()
-    _check(load().sw_run_noalloc(ctypes.byref(cp), _ptr(state), int(nsteps), _stream(stream)),
-           "sw_run_noalloc")
+    return _check(load().sw_run_noalloc(ctypes.byref(cp), _ptr(state), int(nsteps), _stream(stream)),
+                  "sw_run_noalloc")
 
 
 class Handle:

@@ -39,7 +39,7 @@ def _setup(prec, count=24, seed=5, hi_exp=14.0, flat_every=0):
     probs, states, init = [], [], []
     for i, it in enumerate(items):
         W = WIDTHS[i % len(WIDTHS)]  # n is a multiple of 256 and >= 1024
-        flags = S.SW_FLAG_FLATTENED if flat_every and i % flat_every == 0 else 0
+        flags = S.SW_FLAG_FLATTENED if flat_every and i % flat_every == 0 else S.SW_FLAG_LENGTHENED
         p = _problem(it, prec, W, flags)
         x = torch.as_tensor(it.planes.reshape(-1), device="cuda")
         probs.append(p)

@@ -1,8 +1,9 @@
 """GPU parity of the two data-structure strategies of Section 4.3 (Fig. 2) for the Euler
-step, through the C ABI: swept lengthened (default), swept flattened (SW_FLAG_FLATTENED:
-two 5-point stages per step on radius-2 windows), per-step flattened (default) and
-per-step lengthened (SW_FLAG_LENGTHENED: four 3-point launches per step) evaluate the
-same per-cell functions and must agree bitwise, and (FP64) with the oracle."""
+step, through the C ABI: swept lengthened (SW_FLAG_LENGTHENED), swept flattened
+(SW_FLAG_FLATTENED: two 5-point stages per step on radius-2 windows; the default when
+W % 4 == 0 and W >= 8), per-step flattened (default) and per-step lengthened
+(SW_FLAG_LENGTHENED: four 3-point launches per step) evaluate the same per-cell
+functions and must agree bitwise, and (FP64) with the oracle."""
 import numpy as np
 import pytest
 
@@ -50,11 +51,13 @@ def _init(kind, n, seed):
 @pytest.mark.parametrize("prec", [S.SW_FP64, S.SW_FP32, S.SW_FP32_COMP])
 def test_four_forms_agree_bitwise(n, W, steps, bc, kind, prec):
     q0, lam = _init(kind, n, seed=n + steps)
-    swept_len = run_gpu(_prob(n, W, lam, bc, S.SW_SWEPT, prec), q0, steps)
+    swept_len = run_gpu(_prob(n, W, lam, bc, S.SW_SWEPT, prec, S.SW_FLAG_LENGTHENED), q0, steps)
+    swept_default = run_gpu(_prob(n, W, lam, bc, S.SW_SWEPT, prec), q0, steps)
     swept_flat = run_gpu(_prob(n, W, lam, bc, S.SW_SWEPT, prec, S.SW_FLAG_FLATTENED), q0, steps)
     per_flat = run_gpu(_prob(n, W, lam, bc, S.SW_PERSTEP, prec), q0, steps)
     per_len = run_gpu(_prob(n, W, lam, bc, S.SW_PERSTEP, prec, S.SW_FLAG_LENGTHENED), q0, steps)
     assert np.array_equal(swept_flat, swept_len)
+    assert np.array_equal(swept_default, swept_len)
     assert np.array_equal(per_len, per_flat)
     assert np.array_equal(swept_len, per_flat)
     if prec == S.SW_FP64 and n <= 4096:
@@ -67,7 +70,7 @@ def test_flattened_launch_count():
     n, W, steps = 4096, 128, 160
     q0, lam = _init("riemann", n, 1)
     import torch
-    for flags in (0, S.SW_FLAG_FLATTENED):
+    for flags in (0, S.SW_FLAG_LENGTHENED, S.SW_FLAG_FLATTENED):
         p = _prob(n, W, lam, S.SW_TRANSMISSIVE, S.SW_SWEPT, S.SW_FP32, flags)
         st = S.to_state(p, torch.as_tensor(q0.reshape(-1), device="cuda"))
         with S.Handle(p) as h:
@@ -80,7 +83,8 @@ def test_flattened_launch_count():
         assert h.sw_last_launch_count() == 40
 
 
-@pytest.mark.parametrize("flags,W,shift", [(0, 64, 37), (S.SW_FLAG_FLATTENED, 64, 37), (S.SW_FLAG_FLATTENED, 128, 6),
+@pytest.mark.parametrize("flags,W,shift", [(S.SW_FLAG_LENGTHENED, 64, 37), (S.SW_FLAG_FLATTENED, 64, 37),
+                                           (S.SW_FLAG_FLATTENED, 128, 6), (0, 32, 37),
                                            (0, 256, 130)])
 def test_translation_invariance_across_seams_bitwise(flags, W, shift):
     # periodic: shifting the initial state by s cells (s not a multiple of W) shifts the result

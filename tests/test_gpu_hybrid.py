@@ -26,7 +26,8 @@ def _heat(n, W, prec, bc, flags=0, r=0.3):
                      flags=flags)
 
 
-def _euler(n, W, prec, bc, lam, flags=0):
+def _euler(n, W, prec, bc, lam, flags=S.SW_FLAG_LENGTHENED):
+    # the host engine runs the lengthened form (Section 4.3) only
     return S.Problem(scheme=S.SW_EULER, precision=prec, boundary=bc, method=S.SW_SWEPT, n=n, dt_dx=lam, gamma=GAMMA,
                      tile_width=W, flags=flags)
 
@@ -108,6 +109,24 @@ def test_hybrid_repeated_calls_and_thread_change():
         h.sw_run(st, 50)                 # then the GPU alone
         got = S.to_fp64(p, st).cpu().numpy().reshape(1, n)
     assert np.array_equal(got, want)
+
+
+def test_hybrid_rejects_flattened_euler_handle():
+    # swept Euler defaults to the flattened form when W allows it; the host share has only
+    # the lengthened sub-steps, so such a handle is refused before anything runs
+    import torch
+    n, W = 1024, 64
+    q0, lam = I.sod(n), I.sod_lambda()
+    for flags in (0, S.SW_FLAG_FLATTENED):
+        p = _euler(n, W, S.SW_FP32, S.SW_TRANSMISSIVE, lam, flags=flags)
+        st = S.to_state(p, torch.as_tensor(q0.reshape(-1), device="cuda"))
+        before = st.clone()
+        with S.Handle(p) as h:
+            with pytest.raises(S.SweptError) as ei:
+                h.sw_run_hybrid(st, 10, 4, 2)
+            assert ei.value.code == S.SW_ERR_BAD_ARG
+        torch.cuda.synchronize()
+        assert torch.equal(st, before)
 
 
 def test_hybrid_rejects_bad_split():
