@@ -58,6 +58,11 @@ def _load():
         lib.orc_heat_run.restype = i32
         lib.orc_heat_modes.argtypes = [i64, f64, i64, i32, pd, pl, pl, i64, pd]
         lib.orc_heat_modes.restype = i32
+        pi32 = ctypes.POINTER(ctypes.c_int32)
+        lib.orc_heat2d_run.argtypes = [i64, i64, f64, f64, i32, i64, pd]
+        lib.orc_heat2d_run.restype = i32
+        lib.orc_heat2d_modes.argtypes = [i64, i64, f64, f64, i64, i32, pd, pl, pl, pi32, pi32, pl, pl, i64, pd]
+        lib.orc_heat2d_modes.restype = i32
         lib.orc_euler_run.argtypes = [i64, f64, f64, i32, i64, pd, pd, pd]
         lib.orc_euler_run.restype = i32
         lib.orc_riemann_star.argtypes = [f64] * 7 + [pd]
@@ -107,6 +112,37 @@ def heat_modes(n: int, r: float, nsteps: int, amps, ks, idx=None) -> np.ndarray:
                                 _dptr(amps), _lptr(ks), _lptr(idx), idx.size, _dptr(out))
     if rc != 0:
         raise RuntimeError(f"orc_heat_modes failed: {rc}")
+    return out
+
+
+def heat2d_run(u0, rx: float, ry: float, nsteps: int, boundary: int = PERIODIC) -> np.ndarray:
+    """2D FTCS heat equation (5-point stencil), naive stepping. ``u0`` has shape (ny, nx)
+    (x fastest). Returns a new array."""
+    u = np.array(u0, dtype=np.float64, copy=True, order="C")
+    assert u.ndim == 2
+    rc = _load().orc_heat2d_run(u.shape[1], u.shape[0], float(rx), float(ry), int(boundary), int(nsteps), _dptr(u))
+    if rc != 0:
+        raise RuntimeError(f"orc_heat2d_run failed: {rc}")
+    return u
+
+
+def heat2d_modes(nx: int, ny: int, rx: float, ry: float, nsteps: int, amps, kx, ky, fx, fy, ii, jj) -> np.ndarray:
+    """Exact discrete 2D FTCS solution of a periodic sum of separable sin/cos modes, at
+    cells (ii[q], jj[q]) (long double)."""
+    amps = np.ascontiguousarray(amps, dtype=np.float64)
+    kx = np.ascontiguousarray(kx, dtype=np.int64)
+    ky = np.ascontiguousarray(ky, dtype=np.int64)
+    fx = np.ascontiguousarray(fx, dtype=np.int32)
+    fy = np.ascontiguousarray(fy, dtype=np.int32)
+    ii = np.ascontiguousarray(ii, dtype=np.int64)
+    jj = np.ascontiguousarray(jj, dtype=np.int64)
+    out = np.empty(ii.size, dtype=np.float64)
+    p32 = ctypes.POINTER(ctypes.c_int32)
+    rc = _load().orc_heat2d_modes(int(nx), int(ny), float(rx), float(ry), int(nsteps), int(amps.size), _dptr(amps),
+                                  _lptr(kx), _lptr(ky), fx.ctypes.data_as(p32), fy.ctypes.data_as(p32), _lptr(ii),
+                                  _lptr(jj), ii.size, _dptr(out))
+    if rc != 0:
+        raise RuntimeError(f"orc_heat2d_modes failed: {rc}")
     return out
 
 

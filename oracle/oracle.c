@@ -125,6 +125,80 @@ int orc_heat_modes(int64_t n, double r, int64_t nsteps, int nmodes,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Heat equation in two dimensions, FTCS with the 5-point stencil: the 2D
+ * extension of the swept rule that Section 6 names as future work. Reading:
+ *   u_ij <- u_ij + ( rx*((u_{i-1,j} + u_{i+1,j}) - 2 u_ij)
+ *                  + ry*((u_{i,j-1} + u_{i,j+1}) - 2 u_ij) ),
+ * every cell from the old level; u[j*nx + i], i along x (fastest). Periodic:
+ * indices wrap in both directions; transmissive: a ghost copies the edge cell.
+ * Written so that swapping x and y (and rx, ry) transposes the result bit for bit,
+ * and a state constant along y evolves, row by row, bit for bit as orc_heat_run
+ * with r = rx (the y-difference is then exactly zero).                       */
+/* ------------------------------------------------------------------------ */
+int orc_heat2d_run(int64_t nx, int64_t ny, double rx, double ry, int boundary, int64_t nsteps, double *u)
+{
+    if (nx < 2 || ny < 2 || nsteps < 0 || !u) return -1;
+    const int64_t n = nx * ny;
+    double *v = (double *)malloc((size_t)n * sizeof(double));
+    if (!v) return -2;
+    double *cur = u, *nxt = v;
+    const int per = boundary == ORC_PERIODIC;
+    for (int64_t s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int64_t j = 0; j < ny; ++j) {
+            const int64_t jd = j > 0 ? j - 1 : (per ? ny - 1 : 0);
+            const int64_t ju = j < ny - 1 ? j + 1 : (per ? 0 : ny - 1);
+            for (int64_t i = 0; i < nx; ++i) {
+                const int64_t il = i > 0 ? i - 1 : (per ? nx - 1 : 0);
+                const int64_t ir = i < nx - 1 ? i + 1 : (per ? 0 : nx - 1);
+                const double c = cur[j * nx + i];
+                const double xd = (cur[j * nx + il] + cur[j * nx + ir]) - 2.0 * c;
+                const double yd = (cur[jd * nx + i] + cur[ju * nx + i]) - 2.0 * c;
+                nxt[j * nx + i] = c + (rx * xd + ry * yd);
+            }
+        }
+        double *t = cur; cur = nxt; nxt = t;
+    }
+    if (cur != u) memcpy(u, cur, (size_t)n * sizeof(double));
+    free(v);
+    return 0;
+}
+
+/* Exact discrete solution of 2D FTCS on a periodic nx x ny grid for a sum of
+ * separable modes u_ij = sum_m a_m f_m(2 pi kx_m i / nx) g_m(2 pi ky_m j / ny),
+ * f, g = sin (flag 0) or cos (flag 1). Each such product is an eigenvector of the
+ * 5-point operator: the x-difference of sin/cos(theta i) is (2 cos theta - 2)
+ * times it, so G = 1 - 4 rx sin^2(pi kx/nx) - 4 ry sin^2(pi ky/ny) and
+ * u^s = sum_m a_m G_m^s f_m g_m. Long double; output at cells (ii[q], jj[q]).  */
+int orc_heat2d_modes(int64_t nx, int64_t ny, double rx, double ry, int64_t nsteps, int nmodes,
+                     const double *amp, const int64_t *kx, const int64_t *ky, const int32_t *fx,
+                     const int32_t *fy, const int64_t *ii, const int64_t *jj, int64_t nidx, double *out)
+{
+    if (nx < 1 || ny < 1 || nmodes < 0 || nidx < 0) return -1;
+    const long double pi = acosl(-1.0L);
+    for (int64_t q = 0; q < nidx; ++q) {
+        long double sum = 0.0L;
+        for (int m = 0; m < nmodes; ++m) {
+            const long double sx = sinl(pi * (long double)kx[m] / (long double)nx);
+            const long double sy = sinl(pi * (long double)ky[m] / (long double)ny);
+            const long double g = 1.0L - 4.0L * (long double)rx * sx * sx - 4.0L * (long double)ry * sy * sy;
+            const long double gs = nsteps == 0 ? 1.0L : powl(g, (long double)nsteps);
+            int64_t ki = (int64_t)(((__int128)kx[m] * ii[q]) % nx);
+            int64_t kj = (int64_t)(((__int128)ky[m] * jj[q]) % ny);
+            if (ki < 0) ki += nx;
+            if (kj < 0) kj += ny;
+            const long double ax = 2.0L * pi * (long double)ki / (long double)nx;
+            const long double ay = 2.0L * pi * (long double)kj / (long double)ny;
+            const long double f = fx[m] ? cosl(ax) : sinl(ax);
+            const long double h = fy[m] ? cosl(ay) : sinl(ay);
+            sum += (long double)amp[m] * gs * f * h;
+        }
+        out[q] = (double)sum;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Euler equations, second-order finite volume with a minmod limiter driven by
  * the pressure ratio (Section 4.2; Section 4.3 / Fig. 2: the state carries
  * Q = {rho, rho u, E} and a pressure ratio, a predictor stage assigns and a

@@ -82,6 +82,44 @@ def heat_r(seed: int, lo: float = 0.1, hi: float = 0.45) -> float:
     return float(uniform(seed, 1, lo, hi, stream=3)[0])
 
 
+@dataclass(frozen=True)
+class HeatModes2D:
+    """Initial state u_ij = sum_m amps[m] f_m(2 pi kx[m] i / nx) g_m(2 pi ky[m] j / ny),
+    f, g = sin when fx / fy is 0, cos when 1; array layout (ny, nx), x fastest."""
+    nx: int
+    ny: int
+    amps: np.ndarray
+    kx: np.ndarray
+    ky: np.ndarray
+    fx: np.ndarray
+    fy: np.ndarray
+
+
+def heat2d_modes(nx: int, ny: int, n_modes: int, seed: int, kmax: int = 32) -> HeatModes2D:
+    """Seeded amplitudes U[-1,1], integer wavenumbers U{1..kmax} per direction, sin or cos."""
+    amps = uniform(seed, n_modes, -1.0, 1.0, stream=31)
+    kx = randint(seed, n_modes, 1, int(min(kmax, max(1, nx // 2))), stream=32)
+    ky = randint(seed, n_modes, 1, int(min(kmax, max(1, ny // 2))), stream=33)
+    fx = randint(seed, n_modes, 0, 1, stream=34).astype(np.int32)
+    fy = randint(seed, n_modes, 0, 1, stream=35).astype(np.int32)
+    return HeatModes2D(nx=nx, ny=ny, amps=amps, kx=kx, ky=ky, fx=fx, fy=fy)
+
+
+def heat2d_initial(modes: HeatModes2D) -> np.ndarray:
+    """Evaluate the separable mode sum on the (ny, nx) grid (angles reduced exactly)."""
+    nx, ny = modes.nx, modes.ny
+    i = np.arange(nx, dtype=np.int64)
+    j = np.arange(ny, dtype=np.int64)
+    u = np.zeros((ny, nx), dtype=np.float64)
+    for a, kx, ky, fx, fy in zip(modes.amps, modes.kx, modes.ky, modes.fx, modes.fy):
+        ax = (2.0 * np.pi / nx) * ((int(kx) * i) % nx).astype(np.float64)
+        ay = (2.0 * np.pi / ny) * ((int(ky) * j) % ny).astype(np.float64)
+        f = np.cos(ax) if fx else np.sin(ax)
+        g = np.cos(ay) if fy else np.sin(ay)
+        u += a * np.outer(g, f)
+    return u
+
+
 # -------------------------------------------------------------------------- euler
 GAMMA = 1.4
 
