@@ -61,8 +61,6 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--configs", action="store_true",
-                    help="instead of the headline, time the other paper-shaped workloads (one JSON line each)")
     return ap.parse_args()
 
 
@@ -331,39 +329,79 @@ def run_ours(args):
            "api": "sw_run_host (pinned host buffers)"}
     h.close()
 
-    # 4) comparisons on the same grid: per-step kernel and the FP32 forms
+    # 4) comparisons (one rank only: the replicas of a multi-GPU run time the headline alone):
+    #    on the same grid, the per-step kernel and the FP32 forms, every form run for the same
+    #    number of steps so that the errors compare like for like; then the other configured
+    #    workloads
     compare = {}
+    if world == 1:
+        compare_legs(args, S, problem, timed_run, u0_dev, best_w, value, final, flush, stream, dev, compare,
+                     modes, r, u0)
+    cpu = compare.pop("_cpu_baseline", None)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "time_steps": STEPS, "tile_width": best_w,
+                   "r": r, "modes": MODES, "parallelism": f"replicas x{world}",
+                   "l2": "flushed (256 MB write) before every timed step; state reset from a device copy"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks, "wall_s_timed_region": wall, "tile_sweep_gcups": sweep, "compare": compare or None,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def compare_legs(args, S, problem, timed_run, u0_dev, best_w, value, final, flush, stream, dev, compare,
+                 modes, r, u0):
+    """Every comparison of the JSON line besides the headline (single-GPU runs)."""
+    import torch
+    world = 1
     outputs = {("fp64", "swept", STEPS): final.cpu()}
     for name, prec in (("fp64", S.SW_FP64), ("fp32", S.SW_FP32), ("fp32_comp", S.SW_FP32_COMP)):
         if name == "fp64":
             w_prec = best_w
         else:  # the same short timed sweep as for FP64
-            rates = {}
-            for W in WIDTHS[2:]:
-                pw = problem(prec, S.SW_SWEPT, W)
-                st = S.to_state(pw, u0_dev)
-                fresh = st.clone()
-                with S.Handle(pw) as hw:
-                    timed_run(hw, st, 64, fresh)
-                    rates[W] = TUNE_STEPS / timed_run(hw, st, TUNE_STEPS, fresh)
-                del st, fresh
-            w_prec = max(rates, key=rates.get)
+            w_prec = tune_heat_width(S, problem, prec, u0_dev, timed_run, WIDTHS[2:], TUNE_STEPS)
         for method in ("swept", "perstep"):
             if name == "fp64" and method == "swept":
                 compare["fp64_swept"] = {"value": value / world, "steps": STEPS, "W": best_w}
                 continue
-            steps = STEPS if method == "swept" else 5000
-            W = w_prec
-            pp = problem(prec, S.SW_SWEPT if method == "swept" else S.SW_PERSTEP, W)
+            pp = problem(prec, S.SW_SWEPT if method == "swept" else S.SW_PERSTEP, w_prec)
             st = S.to_state(pp, u0_dev)
             fresh = st.clone()
             with S.Handle(pp) as hh:
-                timed_run(hh, st, min(steps, 256), fresh)  # warm-up
-                t = timed_run(hh, st, steps, fresh)
-            compare[f"{name}_{method}"] = {"value": N * steps / t / 1e9, "steps": steps,
-                                           "W": W if method == "swept" else None}
-            outputs[(name, method, steps)] = S.to_fp64(pp, st)[0].cpu()
+                timed_run(hh, st, 256, fresh)  # warm-up
+                t = timed_run(hh, st, STEPS, fresh)
+            compare[f"{name}_{method}"] = {"value": N * STEPS / t / 1e9, "steps": STEPS,
+                                           "W": w_prec if method == "swept" else None}
+            outputs[(name, method, STEPS)] = S.to_fp64(pp, st)[0].cpu()
             del st, fresh
+
+    # the oracle's share of the configured workloads below, computed from the seeded
+    # inputs alone in spawned processes while the GPU legs run (joined before any leg
+    # that uses the host cores)
+    side = OracleSide(True)
+
+    # heat precision workload: N = 2^22, r = 0.4, 100,000 steps, three precisions
+    compare["heat_precision_n2^22"] = heat_precision_leg(S, timed_run)
+    # Euler workloads: Sod N = 2^20, 20,000 steps; 64 random Riemann segments, N = 2^22
+    sod_out = euler_leg(S, timed_run, "sod")
+    rie_out = euler_leg(S, timed_run, "riemann")
+    # the swept rule in two dimensions (heat, 8192 x 8192)
+    compare["heat2d_8192^2"] = heat2d_leg(S, flush, stream)
+    # batched: 4096 problems at the configured 10,000 steps
+    batch_leg, batch_out = batched_leg(S, stream)
+    compare["batched_4096"] = batch_leg
+
+    side.join()  # the host cores are needed by the legs below
+    finish_euler_leg(compare, "euler_sod_n2^20", sod_out, side.result("sod"))
+    finish_euler_leg(compare, "euler_riemann_n2^22", rie_out, side.result("riemann"))
+    finish_batched_leg(compare["batched_4096"], batch_out, side.result("batch"))
+
     # small grid: the launch-latency-bound workload (N = 16384, r = 1/4, 8 modes, 1000 steps, W = 64)
     small = {}
     n_s, steps_s = 16384, 1000
@@ -390,25 +428,6 @@ def run_ours(args):
     small["speedup_fp64_graphs"] = small["fp64_perstep_graph"]["ms"] / small["fp64_swept_w64_graph"]["ms"]
     small["speedup_fp32_graphs"] = small["fp32_perstep_graph"]["ms"] / small["fp32_swept_w128_graph"]["ms"]
     compare["small_grid_n16384_1000_steps"] = small
-
-    # batched: 4096 independent problems (half heat, half Euler, lengths 2^10..2^18), FP32 hi/lo,
-    # autotuned widths, one persistent launch from a CUDA graph; a 200-step run
-    from paper_1811_08282_gb300 import batched
-    items = batched.default_items(4096, seed=7)
-    bt = batched.build(items, 200)
-    bt.batch.sw_batch_run()
-    bt.batch.sw_batch_status()
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    bt.batch.sw_batch_run(stream)
-    b.record(stream)
-    b.synchronize()
-    tb = a.elapsed_time(b) / 1e3
-    compare["batched_4096"] = {"value": bt.cells * 200 / tb / 1e9, "unit": "Gcell-steps/s", "cells": bt.cells,
-                               "steps": 200, "ms": tb * 1e3, "items": bt.batch.sw_batch_items(),
-                               "status": bt.batch.sw_batch_status(), "precision": "fp32_comp"}
-    bt.batch.close()
 
     # FP64 conservation sums (fixed-order tree) over the N = 2^24 state: the whole call,
     # two reduction launches and the 8-byte read-back, timed on the stream (L2 flushed)
@@ -473,26 +492,444 @@ def run_ours(args):
     compare["speedup_swept_over_perstep_fp32_comp"] = (compare["fp32_comp_swept"]["value"]
                                                         / compare["fp32_comp_perstep"]["value"])
 
-    # 5) CPU baseline (rank 0 only): the FP64 oracle on the host cores, bounded
-    #    sample; also states each result's error against the oracle's closed form.
-    cpu = None
-    if rank == 0 and world == 1:
-        cpu = cpu_baseline_leg(modes, r, u0, outputs, compare)
+    # 5) CPU baseline: the FP64 oracle on the host cores, bounded sample; also states each
+    #    result's error against the oracle's closed form.
+    compare["_cpu_baseline"] = cpu_baseline_leg(modes, r, u0, outputs, compare)
 
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N, "time_steps": STEPS, "tile_width": best_w,
-                   "r": r, "modes": MODES, "parallelism": f"replicas x{world}",
-                   "l2": "flushed (256 MB write) before every timed step; state reset from a device copy"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks, "wall_s_timed_region": wall, "tile_sweep_gcups": sweep, "compare": compare,
-    }
-    if rank == 0:
-        print(json.dumps(line))
-    if world > 1:
-        torch.distributed.destroy_process_group()
+
+# ------------------------------------------------------------------ configured workloads
+HEAT4_N, HEAT4_STEPS, HEAT4_R, HEAT4_SEED = 1 << 22, 100_000, 0.4, 4
+SOD_N, SOD_STEPS = 1 << 20, 20_000
+RIE_N, RIE_SEGS, RIE_SEED, RIE_STEPS = 1 << 22, 64, 4, 4_000
+RIE_WINDOWS, RIE_WINDOW_CELLS = 4, 2048
+BATCH_COUNT, BATCH_SEED, BATCH_STEPS = 4096, 7, 10_000
+BATCH_SUBSET, BATCH_SUBSET_MAX_N = 16, 1536  # per scheme: the first items of at most this length
+EULER_WIDTHS = (256, 512, 1024)
+PREC_NAMES = ("fp64", "fp32", "fp32_comp")
+
+
+def tune_heat_width(S, problem, prec, x_dev, timed_run, widths, steps):
+    """Fastest W on a short timed run of the real initial state (Section 6's advice)."""
+    rates = {}
+    for W in widths:
+        pw = problem(prec, S.SW_SWEPT, W)
+        st = S.to_state(pw, x_dev)
+        fresh = st.clone()
+        with S.Handle(pw) as hw:
+            timed_run(hw, st, 64, fresh)
+            rates[W] = steps / timed_run(hw, st, steps, fresh)
+        del st, fresh
+    return max(rates, key=rates.get)
+
+
+def norm_errors(got, ref, names):
+    """Norm-relative max and L2 error per variable (max|g - o| / max|o|, ||g - o|| / ||o||)."""
+    import numpy as np
+    out = {}
+    for v, nm in enumerate(names):
+        d = np.abs(got[v] - ref[v])
+        out[nm] = {"max_rel": float(d.max() / max(np.abs(ref[v]).max(), 1e-300)),
+                   "l2_rel": float(np.linalg.norm(d) / max(np.linalg.norm(ref[v]), 1e-300))}
+    return out
+
+
+def euler_quality(q, gamma=1.4):
+    """Positivity and monotonicity of an Euler state (3, n): the smallest density and
+    pressure, the total variation of both, and the number of local extrema of density
+    whose two sides both exceed 1e-5 of its range (oscillations above rounding level)."""
+    import numpy as np
+    rho, m, E = q
+    p = (gamma - 1.0) * (E - 0.5 * m * (m / rho))
+    drho = np.diff(rho)
+    tol = 1e-5 * max(float(rho.max() - rho.min()), 1e-300)
+    a, b = drho[:-1], drho[1:]
+    ext = int(np.count_nonzero((a * b < 0) & (np.minimum(np.abs(a), np.abs(b)) > tol)))
+    return {"min_rho": float(rho.min()), "min_p": float(p.min()), "tv_rho": float(np.abs(drho).sum()),
+            "tv_p": float(np.abs(np.diff(p)).sum()), "extrema_rho": ext,
+            "finite": bool(np.isfinite(q).all())}
+
+
+def heat_precision_leg(S, timed_run):
+    """Heat, N = 2^22, r = 0.4, 100,000 steps (32 modes): swept and per-step in FP64, FP32
+    and FP32 hi/lo, each with its error against the oracle's closed form (sampled cells)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1811_08282_gb300 import inputs as I
+    n, steps = HEAT4_N, HEAT4_STEPS
+    modes = I.heat_modes(n, 32, seed=HEAT4_SEED)
+    x = torch.as_tensor(I.heat_initial(modes), device="cuda")
+    idx = np.linspace(0, n - 1, 8192).astype(np.int64)
+    want = oracle.heat_modes(n, HEAT4_R, steps, modes.amps, modes.ks, idx)
+
+    def problem(prec, method, W):
+        return S.Problem(scheme=S.SW_HEAT, precision=prec, boundary=S.SW_PERIODIC, method=method, n=n,
+                         r=HEAT4_R, tile_width=W if method == S.SW_SWEPT else 0)
+    res = {"n": n, "steps": steps, "r": HEAT4_R, "modes": 32, "unit": "Gcell-updates/s",
+           "error": "norm-relative max over 8192 sampled cells vs the oracle's exact discrete solution"}
+    for pn, prec in zip(PREC_NAMES, (S.SW_FP64, S.SW_FP32, S.SW_FP32_COMP)):
+        W = tune_heat_width(S, problem, prec, x, timed_run, (128, 256, 512, 1024), 2048)
+        form = {"W": W}
+        for method in ("swept", "perstep"):
+            p = problem(prec, S.SW_SWEPT if method == "swept" else S.SW_PERSTEP, W)
+            st = S.to_state(p, x)
+            fresh = st.clone()
+            with S.Handle(p) as h:
+                timed_run(h, st, 256, fresh)
+                t = timed_run(h, st, steps, fresh)
+            got = S.to_fp64(p, st)[0].cpu().numpy()[idx]
+            form[method] = n * steps / t / 1e9
+            form[f"err_vs_oracle_{method}"] = float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
+            del st, fresh
+        form["speedup"] = form["swept"] / form["perstep"]
+        res[pn] = form
+    return res
+
+
+H2D_N, H2D_STEPS, H2D_R, H2D_SEED = 8192, 2048, 0.2, 6
+H2D_FLOPS_PER_UPDATE = 10  # a + b, d + e, fma(-2, u, .) x 2, fma(ry, ., u), fma(rx, ., .)
+H2D_FP64_INST_PER_UPDATE = 6
+
+
+def heat2d_leg(S, flush, stream):
+    """Heat in two dimensions (the 5-point extension of Section 6's future work): periodic
+    8192 x 8192, rx = ry = 0.2, 16 separable modes, 2048 steps; per precision the swept run
+    (W tuned on short runs) against the per-step kernel, the error against the oracle's
+    exact mode solution at sampled cells (relative to the initial maximum), and for FP64 the
+    roofline of one swept phase (a bridges and an octahedra launch) from traced launches."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1811_08282_gb300 import inputs as I
+    n, steps = H2D_N, H2D_STEPS
+    m = I.heat2d_modes(n, n, 16, seed=H2D_SEED, kmax=16)
+    u0 = I.heat2d_initial(m)
+    rng = np.random.default_rng(1)
+    ii, jj = rng.integers(0, n, 4096), rng.integers(0, n, 4096)
+    want = oracle.heat2d_modes(n, n, H2D_R, H2D_R, steps, m.amps, m.kx, m.ky, m.fx, m.fy, ii, jj)
+    umax = float(np.abs(u0).max())
+    x64 = torch.as_tensor(u0.reshape(-1), device="cuda")
+
+    def run(p, nsteps, trace=0):
+        st = x64.to(torch.float64 if p.precision == S.SW_FP64 else torch.float32).clone()
+        fresh = st.clone()
+        with S.Handle2D(p) as h:
+            h.sw2d_run(st, min(nsteps, 64))
+            st.copy_(fresh)
+            if trace:
+                h.sw2d_set_timing(trace)
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.sw2d_run(st, nsteps, stream)
+            b.record(stream)
+            b.synchronize()
+            launches = h.sw2d_last_launch_count()
+            traced = h.sw2d_launch_times() if trace else []
+        return a.elapsed_time(b) / 1e3, st, launches, traced
+
+    res = {"workload": f"heat 2D FTCS periodic {n}x{n}, rx=ry={H2D_R}, 16 modes, {steps} steps", "unit":
+           "Gcell-updates/s", "error": "max |got - exact| / max |initial| over 4096 sampled cells"}
+    for pn, prec, widths in (("fp64", S.SW_FP64, (32, 64, 96)), ("fp32", S.SW_FP32, (32, 64, 128))):
+        rates = {W: 128 / run(S.Heat2D(precision=prec, method=S.SW_SWEPT, tile_width=W, nx=n, ny=n, rx=H2D_R,
+                                       ry=H2D_R), 128)[0] for W in widths}
+        W = max(rates, key=rates.get)
+        ps = S.Heat2D(precision=prec, method=S.SW_SWEPT, tile_width=W, nx=n, ny=n, rx=H2D_R, ry=H2D_R)
+        ts, st, ls, traced = run(ps, steps, trace=2 * steps // (W // 2) + W)
+        got = st.double().cpu().numpy().reshape(n, n)[jj, ii]
+        tp, stp, lp, _ = run(S.Heat2D(precision=prec, method=S.SW_PERSTEP, nx=n, ny=n, rx=H2D_R, ry=H2D_R), steps)
+        form = {"W": W, "swept": n * n * steps / ts / 1e9, "perstep": n * n * steps / tp / 1e9, "speedup": tp / ts,
+                "launches_swept": ls, "launches_perstep": lp, "swept_equals_perstep": bool(torch.equal(st, stp)),
+                "err_vs_oracle": float(np.abs(got - want).max() / umax),
+                "tile_sweep": {str(k): n * n * 128 / (128 / v) / 1e9 for k, v in rates.items()}}
+        # one swept phase: a bridges launch (kind 1) and an octahedra launch (kind 2)
+        br = [ms for ms, k in traced if k == 1]
+        oc = [ms for ms, k in traced if k == 2]
+        if br and oc:
+            phase_s = (statistics.mean(br) + statistics.mean(oc)) / 1e3
+            updates = n * n * (W // 2)
+            form["phase_ms"] = phase_s * 1e3
+            form["octahedra_share_of_phase"] = statistics.mean(oc) / (statistics.mean(br) + statistics.mean(oc))
+            if prec == S.SW_FP64:
+                achieved = updates * H2D_FLOPS_PER_UPDATE / phase_s / 1e12
+                ceiling = FP64_INST_PER_S / H2D_FP64_INST_PER_UPDATE * H2D_FLOPS_PER_UPDATE / 1e12
+                res["roofline"] = {"bound": "fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                   "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                                   "kernel": f"k2d_bridges<double> + k2d_octa<double> (one swept phase, W = {W})",
+                                   "flops_per_update": H2D_FLOPS_PER_UPDATE,
+                                   "mix_ceiling": ceiling, "frac_of_mix_ceiling": achieved / ceiling,
+                                   "peak_source": "FP64 pipe 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal); "
+                                                  "mix_ceiling: 6 FP64 instructions per update (2 add, 4 FMA)"}
+        res[pn] = form
+    return res
+
+
+def _euler_case(kind):
+    from paper_1811_08282_gb300 import inputs as I
+    if kind == "sod":
+        return dict(n=SOD_N, steps=SOD_STEPS, q0=I.sod(SOD_N), lam=I.sod_lambda(), periodic=False,
+                    workload="Euler Sod N=2^20, 20000 steps, transmissive, CFL 0.4")
+    n = RIE_N
+    return dict(n=n, steps=RIE_STEPS, q0=I.riemann_initial(I.riemann_segments(n, RIE_SEGS, RIE_SEED)),
+                lam=I.riemann_lambda(), periodic=True,
+                workload=f"Euler N=2^22, {RIE_SEGS} random Riemann segments (rho, p log-U[0.1,1], u U[-0.5,0.5]), "
+                         f"{RIE_STEPS} steps, periodic, CFL 0.4")
+
+
+def euler_leg(S, timed_run, kind):
+    """One Euler workload: per precision, swept (default form, W tuned on short runs of the
+    real state) against per-step, the same steps; returns rates and the final states."""
+    import numpy as np
+    import torch
+    from paper_1811_08282_gb300 import inputs as I
+    c = _euler_case(kind)
+    n, steps = c["n"], c["steps"]
+    x = torch.as_tensor(c["q0"].reshape(-1), device="cuda")
+    bc = S.SW_PERIODIC if c["periodic"] else S.SW_TRANSMISSIVE
+
+    def problem(prec, method, W, flags=0):
+        return S.Problem(scheme=S.SW_EULER, precision=prec, boundary=bc, method=method, n=n, dt_dx=c["lam"],
+                         gamma=I.GAMMA, tile_width=W if method == S.SW_SWEPT else 0, flags=flags)
+
+    def run(p, nsteps, warm=8):
+        st = S.to_state(p, x)
+        fresh = st.clone()
+        with S.Handle(p) as h:
+            timed_run(h, st, warm, fresh)
+            t = timed_run(h, st, nsteps, fresh)
+            rc = h.sw_sync_status()
+            launches = h.sw_last_launch_count()
+        if rc < 0:
+            raise S.SweptError(rc, f"euler {kind}")
+        return t, S.to_fp64(p, st).cpu().numpy().reshape(3, n), launches
+
+    out = {"case": c, "forms": {}, "states": {}}
+    for pn, prec in zip(PREC_NAMES, (S.SW_FP64, S.SW_FP32, S.SW_FP32_COMP)):
+        probe = max(16, min(256, int(2e9 / n / (40 if prec == S.SW_FP64 else 1))))  # ~0.1 s per probe run
+        rates = {W: probe / run(problem(prec, S.SW_SWEPT, W), probe, warm=4)[0] for W in EULER_WIDTHS}
+        W = max(rates, key=rates.get)
+        ts, xs, ls = run(problem(prec, S.SW_SWEPT, W), steps)
+        tp, xp, lp = run(problem(prec, S.SW_PERSTEP, 0), steps)
+        form = {"W": W, "form": "flattened" if W % 4 == 0 else "lengthened",
+                "swept": n * steps / ts / 1e9, "perstep": n * steps / tp / 1e9, "speedup": tp / ts,
+                "launches_swept": ls, "launches_perstep": lp, "swept_equals_perstep": bool(np.array_equal(xs, xp))}
+        if prec != S.SW_FP64:
+            # the lengthened swept form at the same width, for the Section 4.3 comparison (same bits)
+            tl, xl, _ = run(problem(prec, S.SW_SWEPT, W, S.SW_FLAG_LENGTHENED), steps)
+            form["swept_lengthened"] = n * steps / tl / 1e9
+            form["lengthened_equals_flattened"] = bool(np.array_equal(xl, xs))
+        out["forms"][pn] = form
+        out["states"][pn] = xs
+        print(f"# euler {kind} {pn} done", file=sys.stderr, flush=True)
+    return out
+
+
+def finish_euler_leg(compare, key, out, oracle_res):
+    """Errors against the oracle, positivity / monotonicity, and the FP64 parity flags."""
+    import numpy as np
+    c = out["case"]
+    n, steps = c["n"], c["steps"]
+    names = ("rho", "m", "E")
+    res = {"workload": c["workload"], "n": n, "steps": steps, "dt_dx": c["lam"], "unit": "Gcell-steps/s",
+           "error": "norm-relative max / L2 per variable"}
+    f64 = out["states"]["fp64"]
+    if not c["periodic"]:
+        # Sod: the oracle on the interface's numerical domain of dependence (4 cells per step
+        # each side; constant beyond it), embedded in the untouched far field: the full field
+        lo, hi = oracle_res["lo"], oracle_res["hi"]
+        ref = c["q0"].copy()
+        ref[:, lo:hi] = oracle_res["q"]
+        res["oracle_cells"] = [int(lo), int(hi)]
+        res["fp64_equals_oracle"] = bool(np.array_equal(f64, ref))
+        q_ref = euler_quality(ref)
+    else:
+        # random Riemann problems: the oracle on sampled windows (each run on its window plus
+        # its domain of dependence); the FP32 forms' full-field error is against the FP64 run
+        wins = oracle_res["windows"]
+        res["oracle_windows"] = [[int(a), int(b)] for a, b, _ in wins]
+        res["fp64_equals_oracle"] = all(np.array_equal(f64[:, a:b], q) for a, b, q in wins)
+        ref = f64
+        q_ref = euler_quality(ref)
+    res["quality_fp64"] = q_ref
+    for pn, form in out["forms"].items():
+        got = out["states"][pn]
+        if pn != "fp64":
+            form["err_vs_oracle" if not c["periodic"] else "err_vs_fp64"] = norm_errors(got, ref, names)
+            if c["periodic"]:
+                g = np.concatenate([got[:, a:b] for a, b, _ in oracle_res["windows"]], axis=1)
+                o = np.concatenate([q for _, _, q in oracle_res["windows"]], axis=1)
+                form["err_vs_oracle_windows"] = norm_errors(g, o, names)
+            q = euler_quality(got)
+            form["quality"] = q
+            form["positive"] = bool(q["finite"] and q["min_rho"] > 0 and q["min_p"] > 0)
+            form["tv_rho_ratio"] = q["tv_rho"] / q_ref["tv_rho"]
+            form["tv_p_ratio"] = q["tv_p"] / q_ref["tv_p"]
+            form["extrema_rho_vs_fp64"] = [q["extrema_rho"], q_ref["extrema_rho"]]
+        else:
+            form["err_vs_oracle"] = "bitwise equal" if res["fp64_equals_oracle"] else "DIFFERS"
+        res[pn] = form
+    compare[key] = res
+
+
+def batched_leg(S, stream):
+    """4096 problems, half heat / half Euler, FP32 hi/lo, lengths log-uniform 2^10..2^18, the
+    configured 10,000 steps in one persistent graph-launched kernel, widths from the tuner."""
+    import torch
+    from paper_1811_08282_gb300 import batched
+    items = batched.default_items(BATCH_COUNT, seed=BATCH_SEED)
+    t0 = time.perf_counter()
+    widths = batched.tune_widths(items)
+    tune_s = time.perf_counter() - t0
+    bt = batched.build(items, BATCH_STEPS, widths=widths)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    bt.batch.sw_batch_run(stream)
+    b.record(stream)
+    b.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    status = bt.batch.sw_batch_status(stream)
+    subset = batch_subset()
+    finals = {i: (items[i].scheme, S.to_fp64(bt.problems[i], bt.states[i]).cpu().numpy().reshape(bt.problems[i].nv, -1))
+              for i in subset}
+    leg = {"value": bt.cells * BATCH_STEPS / t / 1e9, "unit": "Gcell-steps/s", "cells": bt.cells,
+           "problems": len(items), "steps": BATCH_STEPS, "seconds": t, "items": bt.batch.sw_batch_items(),
+           "status": status, "precision": "fp32_comp", "tune_s": tune_s,
+           "widths": {k: {"cap": v[0], "flags": v[1]} for k, v in widths.items()}}
+    bt.batch.close()
+    return leg, finals
+
+
+def batch_subset():
+    """The seeded subset the oracle checks: the first BATCH_SUBSET heat (even index) and Euler
+    (odd index) problems of at most BATCH_SUBSET_MAX_N cells, in the batch's own order."""
+    from paper_1811_08282_gb300 import inputs as I
+    ns = I.batch_lengths(BATCH_COUNT, BATCH_SEED)
+    out = []
+    for parity in (0, 1):
+        out += [i for i in range(parity, BATCH_COUNT, 2) if ns[i] <= BATCH_SUBSET_MAX_N][:BATCH_SUBSET]
+    return out
+
+
+def finish_batched_leg(leg, finals, oracle_res):
+    """Each subset problem's error against the oracle: heat relative to the initial state's
+    largest magnitude (10,000 steps decay the short problems' modes by up to ~1e-8, so the
+    final state's own size says nothing about rounding); Euler norm-relative max and L2 per
+    variable (the worst variable)."""
+    import numpy as np
+    from paper_1811_08282_gb300 import inputs as I
+    idx = sorted(finals)
+    init = {i: it.planes for i, it in zip(idx, I.batch_problems(BATCH_COUNT, BATCH_SEED, indices=idx))}
+    errs = {"heat": [], "euler": []}
+    l2s = []
+    for i, (scheme, got) in finals.items():
+        want = oracle_res[i]
+        if scheme == "heat":
+            errs[scheme].append(float(np.abs(got - want).max() / np.abs(init[i]).max()))
+        else:
+            errs[scheme].append(float((np.abs(got - want).max(axis=1) / np.abs(want).max(axis=1)).max()))
+            l2s.append(float((np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)).max()))
+    leg["subset_vs_oracle"] = {
+        "heat": {"problems": len(errs["heat"]), "max_abs_over_initial_max": max(errs["heat"]),
+                 "median": float(np.median(errs["heat"]))},
+        "euler": {"problems": len(errs["euler"]), "max_rel_max": max(errs["euler"]),
+                  "max_rel_median": float(np.median(errs["euler"])), "l2_rel_max": max(l2s),
+                  "l2_rel_median": float(np.median(l2s))}}
+    leg["subset_rule"] = (f"first {BATCH_SUBSET} heat and {BATCH_SUBSET} Euler problems of at most "
+                          f"{BATCH_SUBSET_MAX_N} cells in batch order, 10,000 steps, against the oracle")
+
+
+# ------------------------------------------------------------------ oracle side jobs
+def _oracle_sod(threads):
+    import numpy as np
+
+    import oracle
+    oracle.set_threads(threads)
+    c = _euler_case("sod")
+    reach = 4 * c["steps"] + 2
+    mid = c["n"] // 2
+    lo, hi = mid - reach - 8, mid + reach + 8
+    q = oracle.euler_run(np.ascontiguousarray(c["q0"][:, lo:hi]), c["lam"], 1.4, c["steps"], oracle.TRANSMISSIVE)
+    return {"lo": lo, "hi": hi, "q": q}
+
+
+def _oracle_riemann(threads):
+    import numpy as np
+
+    import oracle
+    from paper_1811_08282_gb300 import inputs as I
+    oracle.set_threads(threads)
+    c = _euler_case("riemann")
+    n, steps = c["n"], c["steps"]
+    reach = 4 * steps + 8
+    # windows centred on seeded segment interfaces, where the waves are
+    seg = n // RIE_SEGS
+    ifaces = I.randint(99, RIE_WINDOWS, 1, RIE_SEGS - 1, stream=5)
+    starts = ifaces * seg - RIE_WINDOW_CELLS // 2
+    wins = []
+    for a in starts:
+        a = int(a)
+        b = a + RIE_WINDOW_CELLS
+        sub = np.ascontiguousarray(np.take(c["q0"], np.arange(a - reach, b + reach), axis=1, mode="wrap"))
+        q = oracle.euler_run(sub, c["lam"], 1.4, steps, oracle.TRANSMISSIVE)
+        wins.append((a, b, q[:, reach:reach + RIE_WINDOW_CELLS].copy()))
+    return {"windows": wins}
+
+
+def _oracle_batch(indices):
+    import oracle
+    from paper_1811_08282_gb300 import inputs as I
+    oracle.set_threads(1)
+    out = {}
+    for i, it in zip(indices, I.batch_problems(BATCH_COUNT, BATCH_SEED, indices=indices)):
+        if it.scheme == "heat":
+            out[i] = oracle.heat_run(it.planes[0], it.r, BATCH_STEPS, oracle.PERIODIC)[None]
+        else:
+            out[i] = oracle.euler_run(it.planes, I.riemann_lambda(), I.GAMMA, BATCH_STEPS, oracle.TRANSMISSIVE)
+    return out
+
+
+class OracleSide:
+    """The oracle results the configured workloads need, computed from the seeded inputs in
+    spawned worker processes (no CUDA there) while the GPU legs run; `join` waits for all."""
+
+    def __init__(self, enabled: bool):
+        self.futs = {}
+        self.res = {}
+        self.ex = None
+        if not enabled:
+            return
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        ncpu = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        self.ex = ProcessPoolExecutor(max_workers=4, mp_context=mp.get_context("spawn"))
+        subset = batch_subset()
+        half = len(subset) // 2
+        # leave two host cores to the process driving the GPU
+        self.futs["sod"] = [self.ex.submit(_oracle_sod, max(1, ncpu - 6))]
+        self.futs["riemann"] = [self.ex.submit(_oracle_riemann, 2)]
+        self.futs["batch"] = [self.ex.submit(_oracle_batch, subset[:half]), self.ex.submit(_oracle_batch, subset[half:])]
+
+    def join(self):
+        if not self.ex:
+            return
+        for k, fs in self.futs.items():
+            parts = [f.result() for f in fs]
+            if k == "batch":
+                merged = {}
+                for part in parts:
+                    merged.update(part)
+                self.res[k] = merged
+            else:
+                self.res[k] = parts[0]
+        self.ex.shutdown()
+        self.ex = None
+
+    def result(self, key):
+        return self.res.get(key)
 
 
 def cpu_baseline_leg(modes, r, u0, outputs, compare):
@@ -507,6 +944,7 @@ def cpu_baseline_leg(modes, r, u0, outputs, compare):
         err = float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
         compare.setdefault(f"{name}_{method}", {})["err_vs_oracle"] = err
     # timing: oracle FTCS stepping on the full grid, a bounded number of steps
+    cores = oracle.num_threads()
     t0 = time.perf_counter()
     oracle.heat_run(u0, r, 2)
     per_step = (time.perf_counter() - t0) / 2
@@ -514,16 +952,42 @@ def cpu_baseline_leg(modes, r, u0, outputs, compare):
     t0 = time.perf_counter()
     oracle.heat_run(u0, r, steps)
     t = time.perf_counter() - t0
-    return {"value": N * steps / t / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    # the same on one core (a shorter sample)
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    oracle.heat_run(u0, r, 2)
+    per_step1 = (time.perf_counter() - t1) / 2
+    steps1 = max(2, min(50, int(5.0 / max(per_step1, 1e-6))))
+    t1 = time.perf_counter()
+    oracle.heat_run(u0, r, steps1)
+    t1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
+    return {"value": N * steps / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"N=2^24, first {steps} of {STEPS} steps (naive FP64 stepping, OpenMP over cells)",
+            "value_1core": N * steps1 / t1 / 1e9,
+            "sample_1core": f"N=2^24, first {steps1} of {STEPS} steps on one thread",
             "cpu": _cpu_model()}
 
 
+ARM_PARTS = {"0xd4f": "Arm Neoverse-V2", "0xd40": "Arm Neoverse-V1", "0xd49": "Arm Neoverse-N2",
+             "0xd0c": "Arm Neoverse-N1", "0xd8f": "Arm Neoverse-V3"}
+
+
 def _cpu_model():
+    """The host CPU's model name (lscpu's "Model name"; on Arm hosts /proc/cpuinfo gives only
+    the part id, named here for the Neoverse cores)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
     try:
         for line in open("/proc/cpuinfo"):
             if line.lower().startswith(("model name", "cpu part")):
-                return line.split(":", 1)[1].strip()
+                v = line.split(":", 1)[1].strip()
+                return f"{ARM_PARTS[v]} (part {v})" if v in ARM_PARTS else v
     except Exception:
         pass
     return None
@@ -564,146 +1028,10 @@ def run_reference(args):
     }))
 
 
-def run_configs(args):
-    """Rates of the paper-shaped workloads besides the headline, each swept and per-step
-    at FP64, FP32 and FP32 hi/lo, with the FP32 forms' error against the FP64 result
-    (the FP64 path is bitwise equal to the oracle for Euler and within 1e-12 of the
-    oracle's closed form for heat; the full-size parity tests check that on these
-    workloads, Euler on the window the waves reach or on a shorter run). One untimed
-    short run per handle first; single timed run per form (long runs)."""
-    import numpy as np
-    import torch
-    from paper_1811_08282_gb300 import build, batched
-    build.build()
-    from paper_1811_08282_gb300 import swept as S, inputs as I
-    rank, local_rank, world = dist_env()
-    if rank != 0:
-        return
-    torch.cuda.set_device(local_rank)
-    precs = {"fp64": S.SW_FP64, "fp32": S.SW_FP32, "fp32_comp": S.SW_FP32_COMP}
-
-    def timed(p, x0, steps, warm=8):
-        st = S.to_state(p, torch.as_tensor(x0.reshape(-1), device="cuda"))
-        fresh = st.clone()
-        with S.Handle(p) as h:
-            h.sw_run(st, warm)
-            st.copy_(fresh)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            h.sw_run(st, steps)
-            b.record()
-            b.synchronize()
-            rc = h.sw_sync_status()
-            launches = h.sw_last_launch_count()
-        if rc < 0:
-            raise S.SweptError(rc, "configs")
-        return a.elapsed_time(b) / 1e3, S.to_fp64(p, st).cpu().numpy().reshape(p.nv, p.n), launches
-
-    def errors(got, ref):
-        out = {}
-        for v in range(ref.shape[0]):
-            d = np.abs(got[v] - ref[v])
-            out[f"v{v}"] = {"max_rel": float(d.max() / np.abs(ref[v]).max()),
-                            "l2_rel": float(np.linalg.norm(d) / np.linalg.norm(ref[v]))}
-        return out
-
-    def best_width(make, x0, steps, widths=(64, 128, 256, 512, 1024)):
-        n = x0.shape[-1]
-        rates = {}
-        for W in widths:
-            if n % W or n < 2 * W:
-                continue
-            t, _, _ = timed(make(W), x0, steps)
-            rates[W] = t
-        return min(rates, key=rates.get)
-
-    def compare(name, make, x0, steps, tune_steps, extra, flat=False):
-        res = {"config": name, "n": x0.shape[-1], "steps": steps, **extra, "forms": {}}
-        ref = None
-        for pn, pv in precs.items():
-            W = best_width(lambda W: make(pv, S.SW_SWEPT, W), x0, tune_steps)
-            ts, xs, ls = timed(make(pv, S.SW_SWEPT, W), x0, steps)
-            tp, xp, lp = timed(make(pv, S.SW_PERSTEP, 0), x0, steps)
-            form = {"W": W, "swept": x0.shape[-1] * steps / ts / 1e9, "perstep": x0.shape[-1] * steps / tp / 1e9,
-                    "speedup": tp / ts, "launches_swept": ls, "launches_perstep": lp,
-                    "swept_equals_perstep": bool(np.array_equal(xs, xp))}
-            if flat:  # Euler: the swept run in the flattened form of Section 4.3 (same bits)
-                Wf = best_width(lambda W: make(pv, S.SW_SWEPT, W, S.SW_FLAG_FLATTENED), x0, tune_steps)
-                tf, xf, _ = timed(make(pv, S.SW_SWEPT, Wf, S.SW_FLAG_FLATTENED), x0, steps)
-                form.update({"W_flattened": Wf, "swept_flattened": x0.shape[-1] * steps / tf / 1e9,
-                             "flattened_equals_lengthened": bool(np.array_equal(xf, xs))})
-            if pn == "fp64":
-                ref = xs
-            else:
-                form["err_vs_fp64"] = errors(xs, ref)
-            res["forms"][pn] = form
-            print(f"# {name} {pn} done", file=sys.stderr, flush=True)
-        res["unit"] = "Gcell-steps/s"
-        print(json.dumps(res), flush=True)
-
-    # small grid: heat N = 16384, r = 0.25, 8 modes, seeds 0-4, 1000 steps, W = 64 vs per-step
-    n, steps = 16384, 1000
-    rows = []
-    for seed in range(5):
-        x0 = I.heat_initial(I.heat_modes(n, 8, seed=seed))[None]
-        row = {}
-        for pn in ("fp64", "fp32"):
-            mk = lambda m, W: S.Problem(scheme=S.SW_HEAT, precision=precs[pn], boundary=S.SW_PERIODIC, method=m,
-                                        n=n, r=0.25, tile_width=W)
-            ts, xs, _ = timed(mk(S.SW_SWEPT, 64), x0, steps)
-            tp, xp, _ = timed(mk(S.SW_PERSTEP, 0), x0, steps)
-            row[pn] = {"swept_ms": ts * 1e3, "perstep_ms": tp * 1e3, "speedup": tp / ts,
-                       "swept_equals_perstep": bool(np.array_equal(xs, xp))}
-        rows.append(row)
-    print(json.dumps({"config": "heat N=16384 r=0.25 8 modes seeds 0-4, 1000 steps, W=64", "seeds": rows,
-                      "mean_speedup_fp64": statistics.mean(r["fp64"]["speedup"] for r in rows),
-                      "mean_speedup_fp32": statistics.mean(r["fp32"]["speedup"] for r in rows)}), flush=True)
-
-    # Euler Sod, N = 2^20, 20,000 steps, transmissive
-    def euler(lam):
-        return lambda pv, m, W, flags=0: S.Problem(
-            scheme=S.SW_EULER, precision=pv, boundary=S.SW_TRANSMISSIVE, method=m,
-            n=1 << 20 if lam == "sod" else 1 << 22, dt_dx=I.sod_lambda() if lam == "sod" else I.riemann_lambda(),
-            gamma=I.GAMMA, tile_width=W, flags=flags)
-    compare("Euler Sod N=2^20, 20000 steps, transmissive", euler("sod"), I.sod(1 << 20), 20_000, 512,
-            {"dt_dx": I.sod_lambda()}, flat=True)
-
-    # precision config: heat N = 2^22, r = 0.4, 100,000 steps; Euler N = 2^22, 64 random Riemann segments
-    n = 1 << 22
-    heat = lambda pv, m, W: S.Problem(scheme=S.SW_HEAT, precision=pv, boundary=S.SW_PERIODIC, method=m, n=n,
-                                      r=0.4, tile_width=W)
-    compare("heat N=2^22 r=0.4, 100000 steps, 32 modes", heat, I.heat_initial(I.heat_modes(n, 32, seed=1))[None],
-            100_000, 4096, {"r": 0.4})
-    compare("Euler N=2^22, 64 random Riemann segments, 20000 steps, transmissive", euler("riemann"),
-            I.riemann_initial(I.riemann_segments(n, 64, 1)), 20_000, 512, {"dt_dx": I.riemann_lambda()}, flat=True)
-
-    # batched: 4096 problems, FP32 hi/lo, tuned widths, 10,000 steps in one persistent launch
-    items = batched.default_items(4096, seed=7)
-    t0 = time.perf_counter()
-    widths = batched.tune_widths(items)
-    tune_s = time.perf_counter() - t0
-    bt = batched.build(items, 10_000, widths=widths)
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record()
-    bt.batch.sw_batch_run()
-    b.record()
-    b.synchronize()
-    t = a.elapsed_time(b) / 1e3
-    print(json.dumps({"config": "batched 4096 problems, lengths log-uniform 2^10..2^18, half heat / half Euler, "
-                      "FP32 hi/lo, 10000 steps", "cells": bt.cells, "widths": widths, "tune_s": tune_s,
-                      "seconds": t, "value": bt.cells * 10_000 / t / 1e9, "unit": "Gcell-steps/s",
-                      "items": bt.batch.sw_batch_items(), "status": bt.batch.sw_batch_status()}), flush=True)
-    bt.batch.close()
-
-
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.configs:
-        run_configs(args)
     else:
         run_ours(args)
 

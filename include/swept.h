@@ -47,8 +47,9 @@ extern "C" {
  * GRAPH, SW_ERR_CORRUPT and sw_debug_corrupt_guard.
  * 3: swept Euler runs default to the flattened form where W allows it;
  * SW_FLAG_LENGTHENED selects the lengthened form for swept runs too; sw_autotune
- * also picks the Euler form. */
-#define SW_ABI_VERSION 3
+ * also picks the Euler form.
+ * 4: the two-dimensional heat entry points sw2d_*. */
+#define SW_ABI_VERSION 4
 
 #if defined(__GNUC__)
 #define SW_API __attribute__((visibility("default")))
@@ -319,6 +320,54 @@ SW_API void sw_batch_destroy(sw_batch *b);
  * forms of Section 4.3 at each W and ORs the faster form's flag into
  * inout->flags. Allocates a temporary state; synchronises `stream`. */
 SW_API int sw_autotune(sw_problem *inout, int64_t probe_steps, void *stream);
+
+/* ---- two dimensions: FTCS heat on an nx x ny grid (the 5-point stencil) ----------
+ * Section 6 names the extension of the swept rule to two dimensions as future work;
+ * this is that extension for the heat equation, built as the product of two 1D swept
+ * decompositions. At the levels between two full levels every cell belongs to one of
+ * four kinds of region, each the product of a 1D lower (widening) or upper
+ * (narrowing) window in x and in y: pyramids (upper x upper, self-contained),
+ * x-bridges (lower x upper) and y-bridges (upper x lower), each importing the two
+ * outermost cells of its neighbours per level on its widening sides, and
+ * octahedra (lower x lower), which import from four bridges and the corners of four
+ * pyramids, reach the full W x W tile and go on to build the next pyramid. One phase
+ * = one bridges launch and one octahedra launch, W/2 levels; the 2-cell-deep strips
+ * travel through HBM between them, as the flanks of the 1D rule do. No cell of any
+ * level is computed twice.
+ * Update, per cell: u' = fma(rx, fma(-2, u, a + b), fma(ry, fma(-2, u, d + e), u)),
+ * a, b the x-neighbours and d, e the y-neighbours (a state constant along y gives the
+ * 1D update bit for bit). State: nx * ny values, row-major, x fastest
+ * (u[j * nx + i]), double (SW_FP64) or float (SW_FP32).
+ * Swept runs are periodic; nx and ny multiples of W with at least two tiles each;
+ * W even, 8 <= W <= the width the shared memory holds (FP64 118, FP32 166); a run
+ * of L steps does floor(L / (W/2)) swept phases and the remaining L mod (W/2) steps
+ * with the per-step kernel (same bits). Per-step runs: periodic or transmissive. */
+typedef struct sw_heat2d {
+    int32_t precision;  /* SW_FP64 or SW_FP32 */
+    int32_t boundary;   /* SW_PERIODIC, or SW_TRANSMISSIVE (per-step only) */
+    int32_t method;     /* SW_SWEPT or SW_PERSTEP */
+    int32_t tile_width; /* W (swept); 0 = the library default (64) */
+    int64_t nx, ny;     /* grid, each >= 4 (swept: >= 2W), nx * ny <= 2^36 */
+    double rx, ry;      /* alpha dt / dx^2 and alpha dt / dy^2, each > 0 */
+} sw_heat2d;
+
+typedef struct sw_handle2d sw_handle2d;
+
+/* Validate and allocate the strip buffers (swept) or a second plane (per-step) on the
+ * current device. Errors: SW_ERR_BAD_ARG, SW_ERR_UNSUPPORTED (W beyond shared
+ * memory), SW_ERR_OOM, SW_ERR_CUDA. SW_WARN_UNSTABLE (and a handle) when
+ * rx + ry > 1/2. */
+SW_API int sw2d_create(const sw_heat2d *p, sw_handle2d **out);
+SW_API void sw2d_destroy(sw_handle2d *h);
+/* Advance `state` (device, layout above) by nsteps in place on `stream`. */
+SW_API int sw2d_run(sw_handle2d *h, void *state, int64_t nsteps, void *stream);
+/* Launches issued by the last sw2d_run, and the tile width in use. */
+SW_API int64_t sw2d_last_launch_count(const sw_handle2d *h);
+SW_API int32_t sw2d_tile_width(const sw_handle2d *h);
+/* Tracing, as sw_set_timing / sw_launch_times (kinds: 0 Up pyramids, 1 bridges,
+ * 2 octahedra, 3 per-step, 4 the last phase's octahedra). */
+SW_API int sw2d_set_timing(sw_handle2d *h, int64_t capacity);
+SW_API int64_t sw2d_launch_times(sw_handle2d *h, float *ms, int32_t *kind, int64_t cap);
 
 SW_API const char *sw_status_string(int status);
 SW_API int sw_abi_version(void);

@@ -4,14 +4,19 @@
     bt = batched.build(batched.default_items(4096, seed=7), nsteps=10_000)
     bt.batch.sw_batch_run(); bt.batch.sw_batch_status()
 
-Tile widths are tuned as one cap per scheme by timing the batch kernel itself on
-short runs of a GPU-filling sample of the items (Section 6's advice: tune on a few
-short runs), then fitted to each problem's length (largest width <= the cap that
-divides it and leaves at least two tiles). For Euler the tuner also picks the
-staging form of Section 4.3, lengthened or flattened (same results). Heat problems
-are periodic, Euler problems transmissive Riemann problems.
+Tile widths are tuned by timing the batch kernel itself on short runs (Section 6's
+advice: tune on a few short runs), either as one cap per scheme (`tune_widths`) or
+per size class, one octave of problem length per class (`tune_classes`), and then
+fitted to each problem's length (largest width <= the cap that divides it and
+leaves at least two tiles). For Euler the tuner also picks the staging form of
+Section 4.3, lengthened or flattened (same results). `tune` runs both and keeps
+the one that times faster on a short run of the whole batch. Heat problems are
+periodic, Euler problems transmissive Riemann problems.
 """
 from __future__ import annotations
+
+import math
+import time
 
 from dataclasses import dataclass, field
 
@@ -25,7 +30,8 @@ class BuiltBatch:
     problems: list
     states: list
     items: list
-    widths: dict = field(default_factory=dict)  # scheme -> (tuned width cap, flags)
+    # scheme -> (width cap, flags), or (scheme, size class) -> (width cap, flags)
+    widths: dict = field(default_factory=dict)
 
     @property
     def cells(self) -> int:
@@ -107,9 +113,103 @@ def build(items, nsteps: int, precision=S.SW_FP32_COMP, widths=None) -> BuiltBat
     widths = widths if widths is not None else tune_widths(items, precision)
     problems, states = [], []
     for it in items:
-        cap, flags = widths[it.scheme] if isinstance(widths[it.scheme], tuple) else (widths[it.scheme], 0)
+        cap, flags = choice(widths, it)
         W = fit_width(it.n, cap, flags)
         p = _problem(it, precision, W, flags)
         problems.append(p)
         states.append(S.to_state(p, torch.as_tensor(it.planes.reshape(-1), device="cuda")))
     return BuiltBatch(S.Batch(problems, states, nsteps), problems, states, items, widths)
+
+
+def size_class(n: int) -> int:
+    """The octave of a problem length: floor(log2 n)."""
+    return int(math.floor(math.log2(n)))
+
+
+def choice(widths: dict, item):
+    """(width cap, flags) for an item from a per-scheme or a per-size-class table."""
+    key = (item.scheme, size_class(item.n))
+    v = widths.get(key, widths.get(item.scheme))
+    if v is None:
+        raise KeyError(f"no width for {key}")
+    return v if isinstance(v, tuple) else (v, 0)
+
+
+def _time_batch(items, table, precision, steps):
+    """Seconds of one run (after an untimed one) of a batch of `items` under `table`, or
+    None when the run did not finish cleanly."""
+    import torch
+    probs, states = [], []
+    for it in items:
+        cap, flags = choice(table, it)
+        p = _problem(it, precision, fit_width(it.n, cap, flags), flags)
+        probs.append(p)
+        states.append(S.to_state(p, torch.as_tensor(it.planes.reshape(-1), device="cuda")))
+    with S.Batch(probs, states, steps) as b:
+        b.sw_batch_run()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.sw_batch_run()
+        e1.record()
+        e1.synchronize()
+        if b.sw_batch_status() != S.SW_OK:
+            return None
+        return e0.elapsed_time(e1) / 1e3
+
+
+def tune_classes(items, precision=S.SW_FP32_COMP, candidates=(128, 256, 512, 1024), sample_cells: int = 1 << 23,
+                 max_problems: int = 2048):
+    """Width cap (and, for Euler, staging form) per (scheme, size class), each chosen by the
+    cell-steps per second of the batch kernel on a short run of that class alone.
+
+    A class's sample is its items in batch order, repeated (as independent problems) until
+    it holds about `sample_cells` cells (at most `max_problems` problems), so that every class is timed GPU-filling: the small
+    classes then measure the throughput they get inside the whole batch, where their few
+    phases overlap the long problems', not the latency of running them alone. Each timed run
+    covers two phases of the widest candidate (heat: 1024 steps; Euler: 256 steps), after an
+    untimed run. Returns {(scheme, class): (cap, flags)}."""
+    table = {}
+    classes = sorted({(it.scheme, size_class(it.n)) for it in items})
+    for scheme, cls in classes:
+        members = [it for it in items if it.scheme == scheme and size_class(it.n) == cls]
+        sample, cells = [], 0
+        while cells < sample_cells and len(sample) < max_problems:
+            it = members[len(sample) % len(members)]
+            sample.append(it)
+            cells += it.n
+        steps = max(candidates) if scheme == "heat" else max(candidates) // 4
+        forms = (S.SW_FLAG_LENGTHENED, S.SW_FLAG_FLATTENED) if scheme == "euler" else (0,)
+        best = None
+        for cap in candidates:
+            if cap > max(it.n for it in members) // 2 and cap != min(candidates):
+                continue  # no problem of the class is long enough for it
+            for flags in forms:
+                t = _time_batch(sample, {scheme: (cap, flags)}, precision, steps)
+                if t is None:
+                    continue
+                rate = cells * steps / t
+                if best is None or rate > best[0]:
+                    best = (rate, (cap, flags))
+        table[(scheme, cls)] = best[1] if best else ((256, 0) if scheme == "heat" else (256, S.SW_FLAG_LENGTHENED))
+    return table
+
+
+def tune(items, precision=S.SW_FP32_COMP, check_steps: int = 1000):
+    """Per-scheme caps and the per-size-class table, each timed on `check_steps` steps of the
+    whole batch; returns (winning table, report)."""
+    t0 = time.perf_counter()
+    per_scheme = tune_widths(items, precision)
+    t1 = time.perf_counter()
+    per_class = tune_classes(items, precision)
+    t2 = time.perf_counter()
+    cells = sum(it.n for it in items)
+    rate_scheme = cells * check_steps / _time_batch(items, per_scheme, precision, check_steps) / 1e9
+    rate_class = cells * check_steps / _time_batch(items, per_class, precision, check_steps) / 1e9
+    winner = per_class if rate_class > rate_scheme else per_scheme
+    report = {"per_scheme": {k: {"cap": v[0], "flags": v[1]} for k, v in per_scheme.items()},
+              "per_class": {f"{k[0]} 2^{k[1]}": {"cap": v[0], "flags": v[1]} for k, v in sorted(per_class.items())},
+              "check_steps": check_steps, "rate_per_scheme": rate_scheme, "rate_per_class": rate_class,
+              "chosen": "per_class" if winner is per_class else "per_scheme",
+              "tune_s_per_scheme": t1 - t0, "tune_s_per_class": t2 - t1}
+    return winner, report

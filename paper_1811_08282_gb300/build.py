@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # must round every operation exactly as the device kernels do
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-Xcompiler", "-ffp-contract=off", "-I" + os.path.join(ROOT, "include")]
-TUS = ["api.cu", "noalloc.cu", "fold.cu", "fold_euler.cu", "batch.cu"]
+TUS = ["api.cu", "noalloc.cu", "fold.cu", "fold_euler.cu", "batch.cu", "heat2d.cu"]
 
 
 def _nvcc() -> str:

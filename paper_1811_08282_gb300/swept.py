@@ -15,7 +15,7 @@ from dataclasses import dataclass
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libswept.so")
 
-ABI_VERSION = 3  # SW_ABI_VERSION of include/swept.h
+ABI_VERSION = 4  # SW_ABI_VERSION of include/swept.h
 SW_HEAT, SW_EULER = 0, 1
 SW_FP64, SW_FP32, SW_FP32_COMP = 0, 1, 2
 SW_PERIODIC, SW_TRANSMISSIVE = 0, 1
@@ -41,6 +41,8 @@ EXPORTS = (
     "sw_set_timing", "sw_launch_times", "sw_run_noalloc",
     "sw_batch_create", "sw_batch_run", "sw_batch_status", "sw_batch_items", "sw_batch_debug",
     "sw_batch_destroy", "sw_autotune", "sw_hybrid_split", "sw_run_hybrid", "sw_debug_corrupt_guard",
+    "sw2d_create", "sw2d_destroy", "sw2d_run", "sw2d_last_launch_count", "sw2d_tile_width", "sw2d_set_timing",
+    "sw2d_launch_times",
 )
 
 
@@ -56,6 +58,19 @@ class sw_problem(ctypes.Structure):
         ("gamma", ctypes.c_double),
         ("tile_width", ctypes.c_int32),
         ("flags", ctypes.c_int32),
+    ]
+
+
+class sw_heat2d(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("boundary", ctypes.c_int32),
+        ("method", ctypes.c_int32),
+        ("tile_width", ctypes.c_int32),
+        ("nx", ctypes.c_int64),
+        ("ny", ctypes.c_int64),
+        ("rx", ctypes.c_double),
+        ("ry", ctypes.c_double),
     ]
 
 
@@ -108,6 +123,13 @@ def load(path: str = LIB_PATH):
         "sw_batch_debug": ([vp, i64, i32], ctypes.c_int),
         "sw_batch_destroy": ([vp], None),
         "sw_autotune": ([P, i64, vp], ctypes.c_int),
+        "sw2d_create": ([ctypes.POINTER(sw_heat2d), ctypes.POINTER(vp)], ctypes.c_int),
+        "sw2d_destroy": ([vp], None),
+        "sw2d_run": ([vp, vp, i64, vp], ctypes.c_int),
+        "sw2d_last_launch_count": ([vp], i64),
+        "sw2d_tile_width": ([vp], i32),
+        "sw2d_set_timing": ([vp, i64], ctypes.c_int),
+        "sw2d_launch_times": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32), i64], i64),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -355,6 +377,77 @@ def sw_autotune(p: Problem, probe_steps: int, stream=None) -> int:
     _check(load().sw_autotune(ctypes.byref(cp), int(probe_steps), _stream(stream)), "sw_autotune")
     p.tile_width = int(cp.tile_width)
     return p.tile_width
+
+
+@dataclass
+class Heat2D:
+    """Python view of ``sw_heat2d``: FTCS heat on an nx x ny grid (state (ny, nx), x fastest)."""
+    precision: int = SW_FP64
+    boundary: int = SW_PERIODIC
+    method: int = SW_SWEPT
+    tile_width: int = 0
+    nx: int = 256
+    ny: int = 256
+    rx: float = 0.2
+    ry: float = 0.2
+
+    def c(self) -> sw_heat2d:
+        return sw_heat2d(int(self.precision), int(self.boundary), int(self.method), int(self.tile_width),
+                         int(self.nx), int(self.ny), float(self.rx), float(self.ry))
+
+
+class Handle2D:
+    """Owner of an ``sw_handle2d`` (strip buffers on the current device)."""
+
+    def __init__(self, problem: Heat2D):
+        self.problem = problem
+        self._cp = problem.c()
+        h = ctypes.c_void_p()
+        rc = load().sw2d_create(ctypes.byref(self._cp), ctypes.byref(h))
+        _check(rc, "sw2d_create")
+        self.warning = rc
+        self._h = h
+
+    def close(self) -> None:
+        if self._h and self._h.value:
+            load().sw2d_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sw2d_run(self, state, nsteps: int, stream=None) -> None:
+        _check(load().sw2d_run(self._h, _ptr(state), int(nsteps), _stream(stream)), "sw2d_run")
+
+    def sw2d_last_launch_count(self) -> int:
+        return int(load().sw2d_last_launch_count(self._h))
+
+    def sw2d_tile_width(self) -> int:
+        return int(load().sw2d_tile_width(self._h))
+
+    def sw2d_set_timing(self, capacity: int) -> None:
+        _check(load().sw2d_set_timing(self._h, int(capacity)), "sw2d_set_timing")
+
+    def sw2d_launch_times(self, cap: int = 1 << 16):
+        """[(ms, kind)] of the last run's traced launches (0 Up, 1 bridges, 2 octahedra,
+        3 per-step, 4 last octahedra)."""
+        ms = (ctypes.c_float * cap)()
+        kind = (ctypes.c_int32 * cap)()
+        cnt = _check(int(load().sw2d_launch_times(self._h, ms, kind, int(cap))), "sw2d_launch_times")
+        return [(float(ms[i]), int(kind[i])) for i in range(cnt)]
+
+
+def sw2d_create(problem: Heat2D) -> Handle2D:
+    return Handle2D(problem)
 
 
 # --------------------------------------------------------------- conveniences
