@@ -289,22 +289,41 @@ def run_ours(args):
     kname = "k_heat_fold" if fold else "k_swept_phase"
     traffic = recorded_traffic(kname, f"{kname}.heat_fp64.n2^24")
     # the register-resident kernel at W = 128 / 256 puts every other cell on the integer
-    # pipes: its ceiling is the busier of the FP64 and ALU pipes for its instruction mix
+    # pipes: its ceiling is the busier of the FP64 and ALU pipes for its instruction mix, at
+    # the pipes' rates measured now on this GPU (chain probes, paper_1811_08282_gb300/peaks.py)
+    try:
+        from paper_1811_08282_gb300 import peaks
+        pipes = peaks.measure()
+    except Exception:
+        pipes = None
+    fp64_rate = pipes["fp64_fma"] if pipes else FP64_INST_PER_S
+    alu_rate = pipes["int_alu"] if pipes else ALU_LANE_INST_PER_S
+    rates_src = "measured (chain probes)" if pipes else "nominal"
     peak, peak_source = FP64_PEAK_TFLOPS, \
         "FP64 1.25 TFLOP/s class: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz (nominal, recipe)"
     fp64_ipu = recorded(kname, f"{kname}.heat_fp64.w{best_w}", "fp64_inst_per_update") if fold else None
     alu_ipu = recorded(kname, f"{kname}.heat_fp64.w{best_w}", "alu_inst_per_update") if fold else None
+    best_split = None
     if fp64_ipu and alu_ipu:
-        ceiling = min(FP64_INST_PER_S / fp64_ipu, ALU_LANE_INST_PER_S / alu_ipu)  # updates/s
+        ceiling = min(fp64_rate / fp64_ipu, alu_rate / alu_ipu)  # updates/s
         peak = ceiling * FLOPS_PER_UPDATE / 1e12
         peak_source = (f"pipe ceiling of the FP64 + integer-pipe kernel, in FP64-equivalent flops (5 per update): "
-                       f"min(FP64 pipe 152 SM x 2/clk x 2.07 GHz / {fp64_ipu:.3f} FP64 instr per update, "
-                       f"ALU pipe 152 SM x 64 lanes/clk x 2.07 GHz / {alu_ipu:.2f} ALU instr per update) "
-                       f"= {ceiling / 1e9:.1f} G updates/s (instruction counts: ncu, profiles/traffic.txt)")
+                       f"min(FP64 pipe {fp64_rate / 1e9:.0f} G instr/s / {fp64_ipu:.3f} FP64 instr per update, "
+                       f"ALU pipe {alu_rate / 1e9:.0f} G lane-instr/s / {alu_ipu:.2f} ALU instr per update) "
+                       f"= {ceiling / 1e9:.1f} G updates/s; pipe rates {rates_src}, instruction counts: ncu, "
+                       f"profiles/traffic.txt")
+        # algorithmic best split: every FP64-pipe update at its 3 instructions plus every
+        # integer-path update at its cost (2 x the per-update average at the half split), both
+        # pipes busy all the time
+        best_split = (fp64_rate / 3 + alu_rate / (2 * alu_ipu)) * FLOPS_PER_UPDATE / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "fp64_pipe_peak": FP64_PEAK_TFLOPS,
                 "frac_of_fp64_pipe_peak": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                "pipe_rates": {k: v / 1e9 for k, v in pipes.items()} if pipes else None,
+                "pipe_rates_unit": "G thread operations/s",
+                "best_split_peak": best_split,
+                "frac_of_best_split": (achieved / best_split) if (achieved and best_split) else None,
                 "kernel": (f"k_heat_fold<{best_w // 32}, FoldF64> (Diamond phases)" if fold
                            else "k_swept_phase<HeatPolicy<FP64>> (Diamond phases)"),
                 "launches_traced": len(diamonds),
@@ -633,7 +652,7 @@ def heat2d_leg(S, flush, stream):
 
     res = {"workload": f"heat 2D FTCS periodic {n}x{n}, rx=ry={H2D_R}, 16 modes, {steps} steps", "unit":
            "Gcell-updates/s", "error": "max |got - exact| / max |initial| over 4096 sampled cells"}
-    for pn, prec, widths in (("fp64", S.SW_FP64, (32, 64, 96)), ("fp32", S.SW_FP32, (32, 64, 128))):
+    for pn, prec, widths in (("fp64", S.SW_FP64, (32, 64)), ("fp32", S.SW_FP32, (32, 64, 128))):
         rates = {W: 128 / run(S.Heat2D(precision=prec, method=S.SW_SWEPT, tile_width=W, nx=n, ny=n, rx=H2D_R,
                                        ry=H2D_R), 128)[0] for W in widths}
         W = max(rates, key=rates.get)
@@ -776,12 +795,14 @@ def finish_euler_leg(compare, key, out, oracle_res):
 
 def batched_leg(S, stream):
     """4096 problems, half heat / half Euler, FP32 hi/lo, lengths log-uniform 2^10..2^18, the
-    configured 10,000 steps in one persistent graph-launched kernel, widths from the tuner."""
+    configured 10,000 steps in one persistent graph-launched kernel. Widths (and the Euler
+    form) from the tuner: one cap per scheme and one per size class (octave of length), each
+    timed on the batch kernel, the faster table on a 1000-step run of the whole batch kept."""
     import torch
     from paper_1811_08282_gb300 import batched
     items = batched.default_items(BATCH_COUNT, seed=BATCH_SEED)
     t0 = time.perf_counter()
-    widths = batched.tune_widths(items)
+    widths, tune_report = batched.tune(items)
     tune_s = time.perf_counter() - t0
     bt = batched.build(items, BATCH_STEPS, widths=widths)
     a = torch.cuda.Event(enable_timing=True)
@@ -797,8 +818,7 @@ def batched_leg(S, stream):
               for i in subset}
     leg = {"value": bt.cells * BATCH_STEPS / t / 1e9, "unit": "Gcell-steps/s", "cells": bt.cells,
            "problems": len(items), "steps": BATCH_STEPS, "seconds": t, "items": bt.batch.sw_batch_items(),
-           "status": status, "precision": "fp32_comp", "tune_s": tune_s,
-           "widths": {k: {"cap": v[0], "flags": v[1]} for k, v in widths.items()}}
+           "status": status, "precision": "fp32_comp", "tune_s": tune_s, "tuner": tune_report}
     bt.batch.close()
     return leg, finals
 

@@ -17,6 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libswept.so")
+PEAKS_LIB = os.path.join(OUT_DIR, "libpeaks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code is compiled without floating-point contraction: the host share of a hybrid run
 # must round every operation exactly as the device kernels do
@@ -33,7 +34,8 @@ def _nvcc() -> str:
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC))] + [os.path.join(ROOT, "include", "swept.h")]
+    return [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f != "peaks.cu"] + \
+        [os.path.join(ROOT, "include", "swept.h")]
 
 
 def _stale() -> bool:
@@ -63,8 +65,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(TUS)) as ex:
+    with ThreadPoolExecutor(max_workers=len(TUS) + 1) as ex:
+        peaks = ex.submit(build_peaks, force)
         objs = list(ex.map(compile_one, TUS))
+        peaks.result()
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -72,6 +76,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
     return LIB
+
+
+def build_peaks(force: bool = False) -> str:
+    """Compile csrc/peaks.cu (the pipe-rate probes, not part of libswept.so) into libpeaks.so."""
+    src = os.path.join(CSRC, "peaks.cu")
+    if not force and os.path.exists(PEAKS_LIB) and os.path.getmtime(PEAKS_LIB) >= os.path.getmtime(src):
+        return PEAKS_LIB
+    os.makedirs(OUT_DIR, exist_ok=True)
+    tmp = PEAKS_LIB + f".tmp{os.getpid()}"
+    cmd = [_nvcc(), *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", src, "-o", tmp, "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for peaks.cu:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
 
 
 if __name__ == "__main__":

@@ -2,6 +2,8 @@
 
     python -m paper_1811_08282_gb300.profile_case --scheme heat --precision fp64 \
         --method swept --n 16777216 --steps 2048 --width 1024 [--repeat 1] [--generic]
+    python -m paper_1811_08282_gb300.profile_case --scheme heat2d --precision fp64 \
+        --nx 4096 --ny 4096 --steps 256 --width 64
 
 Inputs are the seeded synthetic states of ``inputs`` (heat: 32 sine modes;
 Euler: Sod, or 64 random Riemann segments with --init riemann). Prints the
@@ -20,7 +22,9 @@ PREC = {"fp64": S.SW_FP64, "fp32": S.SW_FP32, "fp32_comp": S.SW_FP32_COMP}
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--scheme", choices=("heat", "euler"), default="heat")
+    ap.add_argument("--scheme", choices=("heat", "euler", "heat2d"), default="heat")
+    ap.add_argument("--nx", type=int, default=4096, help="heat2d: grid width")
+    ap.add_argument("--ny", type=int, default=4096, help="heat2d: grid height")
     ap.add_argument("--precision", choices=tuple(PREC), default="fp64")
     ap.add_argument("--method", choices=("swept", "perstep"), default="swept")
     ap.add_argument("--boundary", choices=("periodic", "transmissive"), default=None)
@@ -37,6 +41,8 @@ def main(argv=None):
     import torch
     from . import build
     build.build()
+    if a.scheme == "heat2d":
+        return run2d(a)
     heat = a.scheme == "heat"
     bc = a.boundary or ("periodic" if heat else "transmissive")
     p = S.Problem(scheme=S.SW_HEAT if heat else S.SW_EULER, precision=PREC[a.precision],
@@ -70,6 +76,33 @@ def main(argv=None):
                       "steps": a.steps, "width": a.width, "generic": a.generic, "flags": a.flags, "launches": launches, "seconds": t,
                       "gcell_updates_per_s": a.n * a.steps / t / 1e9, "status": rc}))
     return 0 if rc == 0 else 1
+
+
+def run2d(a) -> int:
+    """The 2D heat case: 16 seeded separable modes, r = a.r in both directions."""
+    import torch
+    p = S.Heat2D(precision=PREC[a.precision], method=S.SW_SWEPT if a.method == "swept" else S.SW_PERSTEP,
+                 tile_width=a.width if a.method == "swept" else 0, nx=a.nx, ny=a.ny, rx=a.r, ry=a.r)
+    x = I.heat2d_initial(I.heat2d_modes(a.nx, a.ny, 16, seed=1, kmax=16))
+    dt = torch.float64 if p.precision == S.SW_FP64 else torch.float32
+    fresh = torch.as_tensor(x.reshape(-1), device="cuda").to(dt)
+    st = fresh.clone()
+    t = None
+    with S.Handle2D(p) as h:
+        for _ in range(a.repeat):
+            st.copy_(fresh)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            h.sw2d_run(st, a.steps)
+            e1.record()
+            e1.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+        launches = h.sw2d_last_launch_count()
+    print(json.dumps({"scheme": "heat2d", "precision": a.precision, "method": a.method, "nx": a.nx, "ny": a.ny,
+                      "steps": a.steps, "width": a.width, "launches": launches, "seconds": t,
+                      "gcell_updates_per_s": a.nx * a.ny * a.steps / t / 1e9}))
+    return 0
 
 
 if __name__ == "__main__":
