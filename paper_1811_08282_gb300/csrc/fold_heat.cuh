@@ -47,6 +47,10 @@ struct FoldF32 {
     static __device__ __forceinline__ V idle() { return 0.f; }
     static __device__ __forceinline__ V load(const T *p, int64_t plane, int64_t i) { return p[i]; }
     static __device__ __forceinline__ void store(T *p, int64_t plane, int64_t i, V x) { p[i] = x; }
+    // entries i, i + 1 (i even) in one 8-byte store
+    static __device__ __forceinline__ void store2(T *p, int64_t plane, int64_t i, V x, V y) {
+        *reinterpret_cast<float2 *>(p + i) = make_float2(x, y);
+    }
 };
 
 struct FoldF64 {
@@ -67,6 +71,10 @@ struct FoldF64 {
     static __device__ __forceinline__ V idle() { return 1.0; }
     static __device__ __forceinline__ V load(const T *p, int64_t plane, int64_t i) { return p[i]; }
     static __device__ __forceinline__ void store(T *p, int64_t plane, int64_t i, V x) { p[i] = x; }
+    // entries i, i + 1 (i even) in one 16-byte store
+    static __device__ __forceinline__ void store2(T *p, int64_t plane, int64_t i, V x, V y) {
+        *reinterpret_cast<double2 *>(p + i) = make_double2(x, y);
+    }
 };
 
 struct FoldComp {
@@ -88,6 +96,11 @@ struct FoldComp {
     static __device__ __forceinline__ void store(T *p, int64_t plane, int64_t i, V x) {
         p[i] = x.h;
         p[plane + i] = x.l;
+    }
+    // entries i, i + 1 (i even) of both planes, one 8-byte store each
+    static __device__ __forceinline__ void store2(T *p, int64_t plane, int64_t i, V x, V y) {
+        *reinterpret_cast<float2 *>(p + i) = make_float2(x.h, y.h);
+        *reinterpret_cast<float2 *>(p + plane + i) = make_float2(x.l, y.l);
     }
 };
 
@@ -288,25 +301,40 @@ __global__ void __launch_bounds__(128) k_heat_fold(FoldArgs<typename C::T> a, He
 #pragma unroll
                 for (int j = 0; j < K; ++j) v[j] = nv[j];
 
-                // flank entries of the finishing diamond at level F + i (j = i)
+                // flank entries of the finishing diamond at level F + i (j = i): the pairs
+                // [2i], [2i + 1] are the cells z = i, i + 1 (left) and z = W - 2 - i, W - 1 - i
+                // (right), adjacent register slots of one lane at every unrolled level but
+                // u = K - 2, where each pair straddles two lanes: one vector store per pair
                 if (Uact && i <= H - 1) {
-                    {   // z = i  -> left flank [2i]
-                        const int s = (u + 1) % K, lz = g + (u + 1) / K;
-                        if (lane == ((lz + shift) & 31)) C::store(dU0, plane, 2 * i, v[s]);
-                    }
-                    {   // z = i + 1 -> left flank [2i + 1]
-                        const int s = (u + 2) % K, lz = g + (u + 2) / K;
-                        if (lane == ((lz + shift) & 31)) C::store(dU0, plane, 2 * i + 1, v[s]);
-                    }
-                    {   // z = W - 2 - i -> right flank [2i]
-                        const int q = K - 3 - u;
-                        const int s = (q % K + K) % K, lz = 31 - g + (q < 0 ? -1 : 0);
-                        if (lane == ((lz + shift + 32) & 31)) C::store(dU1, plane, 2 * i, v[s]);
-                    }
-                    {   // z = W - 1 - i -> right flank [2i + 1]
-                        const int q = K - 2 - u;
-                        const int s = (q % K + K) % K, lz = 31 - g + (q < 0 ? -1 : 0);
-                        if (lane == ((lz + shift + 32) & 31)) C::store(dU1, plane, 2 * i + 1, v[s]);
+                    if (u != K - 2) {
+                        {   // left: slots (u + 1) % K, (u + 2) % K of lane g + (u + 1) / K
+                            const int s = (u + 1) % K, lz = g + (u + 1) / K;
+                            if (lane == ((lz + shift) & 31)) C::store2(dU0, plane, 2 * i, v[s], v[s + 1]);
+                        }
+                        {   // right: slots q, q + 1 (q = K - 3 - u mod K) of lane 31 - g (- 1 if q < 0)
+                            const int q = K - 3 - u;
+                            const int s = (q % K + K) % K, lz = 31 - g + (q < 0 ? -1 : 0);
+                            if (lane == ((lz + shift + 32) & 31)) C::store2(dU1, plane, 2 * i, v[s], v[s + 1]);
+                        }
+                    } else {
+                        {   // z = i  -> left flank [2i]
+                            const int s = (u + 1) % K, lz = g + (u + 1) / K;
+                            if (lane == ((lz + shift) & 31)) C::store(dU0, plane, 2 * i, v[s]);
+                        }
+                        {   // z = i + 1 -> left flank [2i + 1]
+                            const int s = (u + 2) % K, lz = g + (u + 2) / K;
+                            if (lane == ((lz + shift) & 31)) C::store(dU0, plane, 2 * i + 1, v[s]);
+                        }
+                        {   // z = W - 2 - i -> right flank [2i]
+                            const int q = K - 3 - u;
+                            const int s = (q % K + K) % K, lz = 31 - g + (q < 0 ? -1 : 0);
+                            if (lane == ((lz + shift + 32) & 31)) C::store(dU1, plane, 2 * i, v[s]);
+                        }
+                        {   // z = W - 1 - i -> right flank [2i + 1]
+                            const int q = K - 2 - u;
+                            const int s = (q % K + K) % K, lz = 31 - g + (q < 0 ? -1 : 0);
+                            if (lane == ((lz + shift + 32) & 31)) C::store(dU1, plane, 2 * i + 1, v[s]);
+                        }
                     }
                 }
                 // the starting diamond's full row (level F): its flank entries j = 0

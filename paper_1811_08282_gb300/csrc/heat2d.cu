@@ -61,13 +61,46 @@ template <> struct Ops2D<float> { using O = OpsF; };
 constexpr int kThreads2D = 256;
 
 // ------------------------------------------------------------------ per-step
+// V consecutive cells of a row as 16-byte vector accesses (VEC) or scalars.
+template <class T, int V, bool VEC> struct RowIO {
+    static __device__ __forceinline__ void load(const T *p, T (&x)[V]) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) x[k] = p[k];
+    }
+    static __device__ __forceinline__ void store(T *p, const T (&x)[V]) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) p[k] = x[k];
+    }
+};
+template <> struct RowIO<float, 4, true> {
+    static __device__ __forceinline__ void load(const float *p, float (&x)[4]) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    }
+    static __device__ __forceinline__ void store(float *p, const float (&x)[4]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    }
+};
+template <> struct RowIO<double, 4, true> {
+    static __device__ __forceinline__ void load(const double *p, double (&x)[4]) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+    }
+    static __device__ __forceinline__ void store(double *p, const double (&x)[4]) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(x[0], x[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(x[2], x[3]);
+    }
+};
+
 // One step over the whole grid: each thread takes V consecutive cells of a row (item
 // = row * (nx / V) + chunk, grid-stride); x-neighbours at the chunk's ends and the
-// rows above and below come through the caches.
-template <class T, int V>
+// rows above and below come through the caches. VEC: the row pieces move as 16-byte
+// vectors (the launcher checks the alignment of the state and of nx).
+template <class T, int V, bool VEC>
 __global__ void __launch_bounds__(kThreads2D) k2d_step(const T *__restrict__ in, T *__restrict__ out, int64_t nx,
                                                        int64_t ny, T rx, T ry, int periodic) {
     using O = typename Ops2D<T>::O;
+    using IO = RowIO<T, V, VEC>;
     const int64_t chunks = nx / V, items = chunks * ny;
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
          it += (int64_t)gridDim.x * blockDim.x) {
@@ -76,12 +109,9 @@ __global__ void __launch_bounds__(kThreads2D) k2d_step(const T *__restrict__ in,
         const int64_t ju = j < ny - 1 ? j + 1 : (periodic ? 0 : ny - 1);
         const T *row = in + j * nx, *rd = in + jd * nx, *ru = in + ju * nx;
         T c[V], d[V], e[V];
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            c[k] = row[i0 + k];
-            d[k] = rd[i0 + k];
-            e[k] = ru[i0 + k];
-        }
+        IO::load(row + i0, c);
+        IO::load(rd + i0, d);
+        IO::load(ru + i0, e);
         const T left = i0 > 0 ? row[i0 - 1] : (periodic ? row[nx - 1] : c[0]);
         const T right = i0 + V < nx ? row[i0 + V] : (periodic ? row[0] : c[V - 1]);
         T o[V];
@@ -91,9 +121,7 @@ __global__ void __launch_bounds__(kThreads2D) k2d_step(const T *__restrict__ in,
             const T b = k < V - 1 ? c[k + 1] : right;
             o[k] = heat2d_update<O>(rx, ry, a, b, c[k], d[k], e[k]);
         }
-        T *orow = out + j * nx;
-#pragma unroll
-        for (int k = 0; k < V; ++k) orow[i0 + k] = o[k];
+        IO::store(out + j * nx + i0, o);
     }
 }
 
@@ -139,18 +167,23 @@ template <class T> struct Frame {
     }
 };
 
-// compute the window [x0, x1] x [y0, y1] at level lev from lev - 1
+// compute the window [x0, x1] x [y0, y1] at level lev from lev - 1: the block's threads
+// run over the window's cells in row-major order (consecutive threads on consecutive
+// cells of a row), so narrow windows keep every lane busy; the row of cell t is
+// umulhi(t, ceil(2^32 / w)), exact while t * w < 2^32 (t < w * h <= 2^16 here).
 template <class T>
 __device__ __forceinline__ void compute_window(const Frame<T> &f, int64_t lev, int x0, int x1, int y0, int y1, T rx,
                                                T ry) {
     using O = typename Ops2D<T>::O;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int y = y0 + warp; y <= y1; y += nw) {
-        for (int x = x0 + lane; x <= x1; x += 32) {
-            const T u = f.at(lev - 1, x, y);
-            f.at(lev, x, y) = heat2d_update<O>(rx, ry, f.at(lev - 1, x - 1, y), f.at(lev - 1, x + 1, y), u,
-                                               f.at(lev - 1, x, y - 1), f.at(lev - 1, x, y + 1));
-        }
+    const unsigned w = (unsigned)(x1 - x0 + 1), cnt = w * (unsigned)(y1 - y0 + 1);
+    const unsigned m = 0xFFFFFFFFu / w + 1u;  // ceil(2^32 / w), w >= 2
+    const T *src = f.s + (int)((lev - 1) & 1) * f.slot;
+    T *dst = f.s + (int)(lev & 1) * f.slot;
+    const int org = (y0 - f.cy + f.H + 1) * f.RS + (x0 - f.cx + f.H + 1);
+    for (unsigned t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const unsigned yy = __umulhi(t, m), xx = t - yy * w;
+        const int q = org + (int)yy * f.RS + (int)xx;
+        dst[q] = heat2d_update<O>(rx, ry, src[q - 1], src[q + 1], src[q], src[q - f.RS], src[q + f.RS]);
     }
 }
 
@@ -418,15 +451,20 @@ int run_perstep2d(sw_handle2d *h, T *state, int64_t steps, cudaStream_t st, int6
     const T rx = (T)h->prob.rx, ry = (T)h->prob.ry;
     T *bufs[2] = {state, reinterpret_cast<T *>(h->plane)};
     const int cap = 152 * 16;
-    const uintptr_t al = reinterpret_cast<uintptr_t>(state);
+    // 16-byte row pieces need the state (the scratch plane is 256-byte aligned) and every
+    // row start on 16 bytes: nx a multiple of 4 cells
+    const bool vec = nx % 4 == 0 && reinterpret_cast<uintptr_t>(state) % 16 == 0;
     for (int64_t s = 0; s < steps; ++s) {
         const T *in = bufs[s & 1];
         T *out = bufs[(s + 1) & 1];
         trace2d_begin(h, launches, 3, st);
-        if (nx % 4 == 0 && al % 32 == 0)
-            k2d_step<T, 4><<<grid2d(nx / 4 * ny, cap), kThreads2D, 0, st>>>(in, out, nx, ny, rx, ry, periodic);
+        if (vec)
+            k2d_step<T, 4, true><<<grid2d(nx / 4 * ny, cap), kThreads2D, 0, st>>>(in, out, nx, ny, rx, ry, periodic);
+        else if (nx % 4 == 0)
+            k2d_step<T, 4, false><<<grid2d(nx / 4 * ny, cap), kThreads2D, 0, st>>>(in, out, nx, ny, rx, ry,
+                                                                                   periodic);
         else
-            k2d_step<T, 1><<<grid2d(nx * ny, cap), kThreads2D, 0, st>>>(in, out, nx, ny, rx, ry, periodic);
+            k2d_step<T, 1, false><<<grid2d(nx * ny, cap), kThreads2D, 0, st>>>(in, out, nx, ny, rx, ry, periodic);
         trace2d_end(h, launches, st);
         ++launches;
     }

@@ -27,14 +27,17 @@ __global__ void __launch_bounds__(256) k_fma_chains(T *out, T a, T b, int iters)
     if (s == T(-1234.5)) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
-// integer ALU: an add and a logical operation per chain step (IADD3 and LOP3)
+// integer ALU: one three-input logical operation (LOP3) per chain step; each chain also
+// reads its neighbour's previous value, so no step can be folded away. (Integer adds
+// may issue on other pipes, so they are left out: this measures the ALU pipe alone.)
 __global__ void __launch_bounds__(256) k_alu_chains(uint32_t *out, uint32_t a, uint32_t b, int iters) {
     uint32_t x0 = threadIdx.x, x1 = x0 * 3u + 1u, x2 = x0 * 5u + 2u, x3 = x0 * 7u + 3u;
     uint32_t x4 = x0 * 11u + 4u, x5 = x0 * 13u + 5u, x6 = x0 * 17u + 6u, x7 = x0 * 19u + 7u;
 #pragma unroll 4
     for (int i = 0; i < iters; ++i) {
-        x0 = (x0 + a) ^ b; x1 = (x1 + a) ^ b; x2 = (x2 + a) ^ b; x3 = (x3 + a) ^ b;
-        x4 = (x4 + a) ^ b; x5 = (x5 + a) ^ b; x6 = (x6 + a) ^ b; x7 = (x7 + a) ^ b;
+        const uint32_t y0 = x0;
+        x0 = (x0 ^ x1) & a; x1 = (x1 ^ x2) | b; x2 = (x2 ^ x3) & a; x3 = (x3 ^ x4) | b;
+        x4 = (x4 ^ x5) & a; x5 = (x5 ^ x6) | b; x6 = (x6 ^ x7) & a; x7 = (x7 ^ y0) | b;
     }
     const uint32_t s = ((x0 ^ x1) + (x2 ^ x3)) ^ ((x4 ^ x5) + (x6 ^ x7));
     if (s == 0x9E3779B9u) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
@@ -62,7 +65,7 @@ double time_ms(K launch) {
 extern "C" {
 
 // Thread-level operations per second of one kind: 0 FP64 FMA, 1 FP32 FMA, 2 integer
-// ALU (IADD3 + LOP3, counted as two). `iters` chain steps per thread; returns < 0 on
+// ALU (LOP3). `iters` chain steps per thread; returns < 0 on
 // a CUDA error. Uses a small scratch buffer of its own (allocated and freed here).
 double pk_rate(int kind, int iters) {
     int dev = 0, sms = 0;
@@ -78,7 +81,6 @@ double pk_rate(int kind, int iters) {
         ms = time_ms([&] { k_fma_chains<float><<<blocks, threads>>>((float *)buf, 0.99999f, 1e-5f, iters); });
     } else {
         ms = time_ms([&] { k_alu_chains<<<blocks, threads>>>((uint32_t *)buf, 0x7F4A7C15u, 0x85EBCA6Bu, iters); });
-        per_step = 16.0;
     }
     cudaFree(buf);
     if (ms <= 0.0) return -1.0;
