@@ -289,39 +289,43 @@ def run_ours(args):
     kname = "k_heat_fold" if fold else "k_swept_phase"
     traffic = recorded_traffic(kname, f"{kname}.heat_fp64.n2^24")
     # the register-resident kernel at W = 128 / 256 puts every other cell on the integer
-    # pipes: its ceiling is the busier of the FP64 and ALU pipes for its instruction mix, at
-    # the pipes' rates measured now on this GPU (chain probes, paper_1811_08282_gb300/peaks.py)
+    # pipes: its ceiling is the busier of the FP64 and ALU pipes for its instruction mix.
+    # `peak` takes the pipes' nominal issue rates (ncu's "% busy" is relative to them); the
+    # rates measured now by the chain probes (paper_1811_08282_gb300/peaks.py) give a second
+    # ceiling beside it, and the algorithmic best split a third.
     try:
         from paper_1811_08282_gb300 import peaks
         pipes = peaks.measure()
     except Exception:
         pipes = None
     fp64_rate = pipes["fp64_fma"] if pipes else FP64_INST_PER_S
-    alu_rate = pipes["int_alu"] if pipes else ALU_LANE_INST_PER_S
-    rates_src = "measured (chain probes)" if pipes else "nominal"
     peak, peak_source = FP64_PEAK_TFLOPS, \
         "FP64 1.25 TFLOP/s class: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz (nominal, recipe)"
     fp64_ipu = recorded(kname, f"{kname}.heat_fp64.w{best_w}", "fp64_inst_per_update") if fold else None
     alu_ipu = recorded(kname, f"{kname}.heat_fp64.w{best_w}", "alu_inst_per_update") if fold else None
-    best_split = None
+    best_split = peak_measured = None
     if fp64_ipu and alu_ipu:
-        ceiling = min(fp64_rate / fp64_ipu, alu_rate / alu_ipu)  # updates/s
+        ceiling = min(FP64_INST_PER_S / fp64_ipu, ALU_LANE_INST_PER_S / alu_ipu)  # updates/s
         peak = ceiling * FLOPS_PER_UPDATE / 1e12
         peak_source = (f"pipe ceiling of the FP64 + integer-pipe kernel, in FP64-equivalent flops (5 per update): "
-                       f"min(FP64 pipe {fp64_rate / 1e9:.0f} G instr/s / {fp64_ipu:.3f} FP64 instr per update, "
-                       f"ALU pipe {alu_rate / 1e9:.0f} G lane-instr/s / {alu_ipu:.2f} ALU instr per update) "
-                       f"= {ceiling / 1e9:.1f} G updates/s; pipe rates {rates_src}, instruction counts: ncu, "
-                       f"profiles/traffic.txt")
+                       f"min(FP64 pipe 152 SM x 2/clk x 2.07 GHz / {fp64_ipu:.3f} FP64 instr per update, "
+                       f"ALU pipe 152 SM x 64 lanes/clk x 2.07 GHz / {alu_ipu:.2f} ALU instr per update) "
+                       f"= {ceiling / 1e9:.1f} G updates/s (nominal issue rates; instruction counts: ncu, "
+                       f"profiles/traffic.txt)")
+        if pipes:
+            peak_measured = min(pipes["fp64_fma"] / fp64_ipu, pipes["int_alu"] / alu_ipu) * FLOPS_PER_UPDATE / 1e12
         # algorithmic best split: every FP64-pipe update at its 3 instructions plus every
         # integer-path update at its cost (2 x the per-update average at the half split), both
-        # pipes busy all the time
-        best_split = (fp64_rate / 3 + alu_rate / (2 * alu_ipu)) * FLOPS_PER_UPDATE / 1e12
+        # pipes busy all the time, at the nominal rates
+        best_split = (FP64_INST_PER_S / 3 + ALU_LANE_INST_PER_S / (2 * alu_ipu)) * FLOPS_PER_UPDATE / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "fp64_pipe_peak": FP64_PEAK_TFLOPS,
                 "frac_of_fp64_pipe_peak": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                "pipe_rates": {k: v / 1e9 for k, v in pipes.items()} if pipes else None,
+                "pipe_rates_measured": {k: v / 1e9 for k, v in pipes.items()} if pipes else None,
                 "pipe_rates_unit": "G thread operations/s",
+                "peak_at_measured_rates": peak_measured,
+                "frac_at_measured_rates": (achieved / peak_measured) if (achieved and peak_measured) else None,
                 "best_split_peak": best_split,
                 "frac_of_best_split": (achieved / best_split) if (achieved and best_split) else None,
                 "kernel": (f"k_heat_fold<{best_w // 32}, FoldF64> (Diamond phases)" if fold
@@ -805,9 +809,9 @@ def batched_leg(S, stream):
     from paper_1811_08282_gb300 import batched
     items = batched.default_items(BATCH_COUNT, seed=BATCH_SEED)
     t0 = time.perf_counter()
-    widths, tune_report = batched.tune(items)
+    widths, threads, tune_report = batched.tune(items)
     tune_s = time.perf_counter() - t0
-    bt = batched.build(items, BATCH_STEPS, widths=widths)
+    bt = batched.build(items, BATCH_STEPS, widths=widths, threads=threads)
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)

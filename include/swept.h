@@ -48,7 +48,7 @@ extern "C" {
  * 3: swept Euler runs default to the flattened form where W allows it;
  * SW_FLAG_LENGTHENED selects the lengthened form for swept runs too; sw_autotune
  * also picks the Euler form.
- * 4: the two-dimensional heat entry points sw2d_*. */
+ * 4: the two-dimensional heat entry points sw2d_*; sw_batch_set_threads. */
 #define SW_ABI_VERSION 4
 
 #if defined(__GNUC__)
@@ -303,6 +303,13 @@ SW_API int sw_batch_status(sw_batch *b, void *stream);
 
 /* Work items per run (for reporting). */
 SW_API int64_t sw_batch_items(const sw_batch *b);
+
+/* Threads per CTA of the persistent kernel: 64, 128 (the default) or 256; each CTA
+ * runs one structure at a time with all its threads, so narrow tiles leave fewer of
+ * them idle with fewer threads and wide ones have more work per level. Synchronises
+ * the device; the next sw_batch_run captures its graph again. Errors: SW_ERR_BAD_ARG,
+ * SW_ERR_CUDA. */
+SW_API int sw_batch_set_threads(sw_batch *b, int32_t threads);
 
 /* Failure-injection hook for tests: set the dependency-wait budget in clock
  * cycles and, if drop_publish != 0, make structure 0 of problem 0 never

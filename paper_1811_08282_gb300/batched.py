@@ -108,7 +108,7 @@ def fit_width(n: int, tuned: int, flags: int = 0) -> int:
     return W
 
 
-def build(items, nsteps: int, precision=S.SW_FP32_COMP, widths=None) -> BuiltBatch:
+def build(items, nsteps: int, precision=S.SW_FP32_COMP, widths=None, threads: int = 128) -> BuiltBatch:
     import torch
     widths = widths if widths is not None else tune_widths(items, precision)
     problems, states = [], []
@@ -118,7 +118,10 @@ def build(items, nsteps: int, precision=S.SW_FP32_COMP, widths=None) -> BuiltBat
         p = _problem(it, precision, W, flags)
         problems.append(p)
         states.append(S.to_state(p, torch.as_tensor(it.planes.reshape(-1), device="cuda")))
-    return BuiltBatch(S.Batch(problems, states, nsteps), problems, states, items, widths)
+    batch = S.Batch(problems, states, nsteps)
+    if threads != 128:
+        batch.sw_batch_set_threads(threads)
+    return BuiltBatch(batch, problems, states, items, widths)
 
 
 def size_class(n: int) -> int:
@@ -135,9 +138,9 @@ def choice(widths: dict, item):
     return v if isinstance(v, tuple) else (v, 0)
 
 
-def _time_batch(items, table, precision, steps):
-    """Seconds of one run (after an untimed one) of a batch of `items` under `table`, or
-    None when the run did not finish cleanly."""
+def _time_batch(items, table, precision, steps, threads=128):
+    """Seconds of one run (after an untimed one) of a batch of `items` under `table`, with
+    `threads` per CTA, or None when the run did not finish cleanly."""
     import torch
     probs, states = [], []
     for it in items:
@@ -146,6 +149,8 @@ def _time_batch(items, table, precision, steps):
         probs.append(p)
         states.append(S.to_state(p, torch.as_tensor(it.planes.reshape(-1), device="cuda")))
     with S.Batch(probs, states, steps) as b:
+        if threads != 128:
+            b.sw_batch_set_threads(threads)
         b.sw_batch_run()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -195,9 +200,10 @@ def tune_classes(items, precision=S.SW_FP32_COMP, candidates=(128, 256, 512, 102
     return table
 
 
-def tune(items, precision=S.SW_FP32_COMP, check_steps: int = 1000):
+def tune(items, precision=S.SW_FP32_COMP, check_steps: int = 500, threads=(64, 128, 256)):
     """Per-scheme caps and the per-size-class table, each timed on `check_steps` steps of the
-    whole batch; returns (winning table, report)."""
+    whole batch, then the threads per CTA of the persistent kernel for the winning table;
+    returns (winning table, threads, report)."""
     t0 = time.perf_counter()
     per_scheme = tune_widths(items, precision)
     t1 = time.perf_counter()
@@ -207,9 +213,19 @@ def tune(items, precision=S.SW_FP32_COMP, check_steps: int = 1000):
     rate_scheme = cells * check_steps / _time_batch(items, per_scheme, precision, check_steps) / 1e9
     rate_class = cells * check_steps / _time_batch(items, per_class, precision, check_steps) / 1e9
     winner = per_class if rate_class > rate_scheme else per_scheme
+    rates_nt = {}
+    for nt in threads:
+        t = rate_scheme if (nt == 128 and winner is per_scheme) else \
+            (rate_class if nt == 128 else None)
+        if t is None:
+            sec = _time_batch(items, winner, precision, check_steps, nt)
+            t = cells * check_steps / sec / 1e9 if sec else 0.0
+        rates_nt[nt] = t
+    best_nt = max(rates_nt, key=rates_nt.get)
     report = {"per_scheme": {k: {"cap": v[0], "flags": v[1]} for k, v in per_scheme.items()},
               "per_class": {f"{k[0]} 2^{k[1]}": {"cap": v[0], "flags": v[1]} for k, v in sorted(per_class.items())},
               "check_steps": check_steps, "rate_per_scheme": rate_scheme, "rate_per_class": rate_class,
               "chosen": "per_class" if winner is per_class else "per_scheme",
-              "tune_s_per_scheme": t1 - t0, "tune_s_per_class": t2 - t1}
-    return winner, report
+              "rate_by_threads_per_cta": rates_nt, "threads_per_cta": best_nt,
+              "tune_s_per_scheme": t1 - t0, "tune_s_per_class": t2 - t1, "tune_s": time.perf_counter() - t0}
+    return winner, best_nt, report

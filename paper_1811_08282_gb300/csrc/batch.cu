@@ -27,7 +27,7 @@ using namespace sw;
 
 namespace {
 
-constexpr int kBatchThreads = 128;
+constexpr int kBatchThreads = 128;  // default threads per CTA (sw_batch_set_threads: 64, 128 or 256)
 constexpr int kChunk = 8;  // structures per work item
 
 struct BatchDesc {
@@ -96,8 +96,10 @@ __device__ __forceinline__ int64_t upper_index(const int64_t *v, int64_t lo, int
     return lo;
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(kBatchThreads, PREC == 0 ? 4 : 8) k_batch(BatchTables t) {
+// NT threads per CTA; the launch bound keeps the register budget per thread of the
+// 128-thread form (64 registers in FP32, 128 in FP64) whatever NT is
+template <int PREC, int NT>
+__global__ void __launch_bounds__(NT, (PREC == 0 ? 4 : 8) * 128 / NT) k_batch(BatchTables t) {
     using HP = HeatPolicy<PREC>;
     using EP = typename EulerPolicyOf<PREC>::type;
     using EF = typename EulerFlatOf<PREC>::type;
@@ -235,6 +237,7 @@ int nsnap_for(int scheme, int prec, bool flat) {
 
 struct sw_batch {
     int precision = 0;
+    int threads = kBatchThreads;  // per CTA of the persistent kernel
     int32_t count = 0;
     int64_t nsteps = 0;
     std::vector<BatchDesc> desc;
@@ -250,6 +253,49 @@ struct sw_batch {
     long long budget = 2000000000LL;  // ~1 s at 2 GHz
     int drop_publish = 0;
 };
+
+namespace {
+
+template <int PREC> const void *kernel_for_nt(int nt) {
+    switch (nt) {
+    case 64: return (const void *)k_batch<PREC, 64>;
+    case 256: return (const void *)k_batch<PREC, 256>;
+    default: return (const void *)k_batch<PREC, 128>;
+    }
+}
+
+const void *batch_kernel(int prec, int nt) {
+    return prec == SW_FP64 ? kernel_for_nt<0>(nt) : prec == SW_FP32 ? kernel_for_nt<1>(nt) : kernel_for_nt<2>(nt);
+}
+
+// The persistent grid for b->threads: every CTA the device can hold at once (items never
+// wait on items taken later, so a smaller resident set is also safe), at most one per item.
+cudaError_t configure_grid(sw_batch *b) {
+    const void *fn = batch_kernel(b->precision, b->threads);
+    cudaError_t e = cudaSuccess;
+    if (b->smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b->threads, b->smem);
+    if (e != cudaSuccess) return e;
+    b->grid = std::max(1, per_sm) * std::max(1, sms);
+    if ((int64_t)b->grid > b->tab.total) b->grid = (int)std::max<int64_t>(b->tab.total, 1);
+    return cudaSuccess;
+}
+
+template <int PREC> void launch_batch(const sw_batch *b, const BatchTables &t, cudaStream_t st) {
+    switch (b->threads) {
+    case 64: k_batch<PREC, 64><<<b->grid, 64, b->smem, st>>>(t); break;
+    case 256: k_batch<PREC, 256><<<b->grid, 256, b->smem, st>>>(t); break;
+    default: k_batch<PREC, 128><<<b->grid, 128, b->smem, st>>>(t); break;
+    }
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -401,21 +447,8 @@ int sw_batch_create(const sw_problem *probs, void *const *states, int32_t count,
     b->tab.flags = reinterpret_cast<int *>(b->d_flags);
     b->tab.queue = reinterpret_cast<unsigned long long *>(b->d_queue);
     b->tab.status = reinterpret_cast<int *>(b->d_status);
-    // persistent grid: every CTA the device can hold at once (items never wait on
-    // items taken later, so a smaller resident set is also safe)
-    const void *fn = prec == SW_FP64 ? (const void *)k_batch<0>
-                   : prec == SW_FP32 ? (const void *)k_batch<1> : (const void *)k_batch<2>;
-    if (b->smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-        if (e != cudaSuccess) return fail(cuda_status_b(e));
-    }
-    int per_sm = 0, dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, b->smem);
+    e = configure_grid(b);
     if (e != cudaSuccess) return fail(cuda_status_b(e));
-    b->grid = std::max(1, per_sm) * std::max(1, sms);
-    if ((int64_t)b->grid > total) b->grid = (int)std::max<int64_t>(total, 1);
     e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return fail(cuda_status_b(e));
     *out = b;
@@ -446,9 +479,9 @@ static cudaError_t batch_enqueue(sw_batch *b, cudaStream_t st) {
     BatchTables t = b->tab;
     t.budget = b->budget;
     t.drop_publish = b->drop_publish;
-    if (b->precision == SW_FP64) k_batch<0><<<b->grid, kBatchThreads, b->smem, st>>>(t);
-    else if (b->precision == SW_FP32) k_batch<1><<<b->grid, kBatchThreads, b->smem, st>>>(t);
-    else k_batch<2><<<b->grid, kBatchThreads, b->smem, st>>>(t);
+    if (b->precision == SW_FP64) launch_batch<0>(b, t, st);
+    else if (b->precision == SW_FP32) launch_batch<1>(b, t, st);
+    else launch_batch<2>(b, t, st);
     return cudaGetLastError();
 }
 
@@ -480,6 +513,22 @@ int sw_batch_status(sw_batch *b, void *stream) {
 }
 
 int64_t sw_batch_items(const sw_batch *b) { return b ? b->tab.total : 0; }
+
+int sw_batch_set_threads(sw_batch *b, int32_t threads) {
+    if (!b || (threads != 64 && threads != 128 && threads != 256)) return SW_ERR_BAD_ARG;
+    cudaError_t e = cudaDeviceSynchronize();  // no launch of the old configuration in flight
+    if (e != cudaSuccess) return cuda_status_b(e);
+    b->threads = threads;
+    e = configure_grid(b);
+    if (e != cudaSuccess) return cuda_status_b(e);
+    if (b->exec) {  // the launch configuration is baked into the graph: capture it again
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+    }
+    return SW_OK;
+}
 
 int sw_autotune(sw_problem *inout, int64_t probe_steps, void *stream) {
     if (!inout || probe_steps <= 0) return SW_ERR_BAD_ARG;

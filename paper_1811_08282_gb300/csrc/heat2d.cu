@@ -180,6 +180,8 @@ __device__ __forceinline__ void compute_window(const Frame<T> &f, int64_t lev, i
     const T *src = f.s + (int)((lev - 1) & 1) * f.slot;
     T *dst = f.s + (int)(lev & 1) * f.slot;
     const int org = (y0 - f.cy + f.H + 1) * f.RS + (x0 - f.cx + f.H + 1);
+    // a thread's cells are independent: unrolled, their shared-memory loads overlap
+#pragma unroll 4
     for (unsigned t = threadIdx.x; t < cnt; t += blockDim.x) {
         const unsigned yy = __umulhi(t, m), xx = t - yy * w;
         const int q = org + (int)yy * f.RS + (int)xx;

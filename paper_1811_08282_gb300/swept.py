@@ -40,7 +40,7 @@ EXPORTS = (
     "sw_last_launch_count", "sw_tile_width", "sw_status_string", "sw_abi_version",
     "sw_set_timing", "sw_launch_times", "sw_run_noalloc",
     "sw_batch_create", "sw_batch_run", "sw_batch_status", "sw_batch_items", "sw_batch_debug",
-    "sw_batch_destroy", "sw_autotune", "sw_hybrid_split", "sw_run_hybrid", "sw_debug_corrupt_guard",
+    "sw_batch_destroy", "sw_batch_set_threads", "sw_autotune", "sw_hybrid_split", "sw_run_hybrid", "sw_debug_corrupt_guard",
     "sw2d_create", "sw2d_destroy", "sw2d_run", "sw2d_last_launch_count", "sw2d_tile_width", "sw2d_set_timing",
     "sw2d_launch_times",
 )
@@ -122,6 +122,7 @@ def load(path: str = LIB_PATH):
         "sw_batch_items": ([vp], i64),
         "sw_batch_debug": ([vp, i64, i32], ctypes.c_int),
         "sw_batch_destroy": ([vp], None),
+        "sw_batch_set_threads": ([vp, i32], ctypes.c_int),
         "sw_autotune": ([P, i64, vp], ctypes.c_int),
         "sw2d_create": ([ctypes.POINTER(sw_heat2d), ctypes.POINTER(vp)], ctypes.c_int),
         "sw2d_destroy": ([vp], None),
@@ -361,6 +362,10 @@ class Batch:
 
     def sw_batch_items(self) -> int:
         return int(load().sw_batch_items(self._b))
+
+    def sw_batch_set_threads(self, threads: int) -> None:
+        """Threads per CTA of the persistent kernel (64, 128 or 256)."""
+        _check(load().sw_batch_set_threads(self._b, int(threads)), "sw_batch_set_threads")
 
     def sw_batch_debug(self, wait_budget_cycles: int, drop_publish: bool) -> None:
         _check(load().sw_batch_debug(self._b, int(wait_budget_cycles), 1 if drop_publish else 0),

@@ -76,6 +76,51 @@ def test_batch_equals_individual_runs(prec, flat_every):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("threads", [64, 256])
+def test_threads_per_cta_give_the_same_bits(threads):
+    # the persistent kernel with 64 or 256 threads per CTA (sw_batch_set_threads) against the
+    # default 128, set before the first run and changed between runs (the graph is re-captured)
+    import torch
+    items, probs, states, init = _setup(S.SW_FP32_COMP, count=20, seed=12, flat_every=2)
+    nsteps = 90
+    with S.Batch(probs, states, nsteps) as b:
+        b.sw_batch_run()
+        assert b.sw_batch_status() == S.SW_OK
+        ref = _read(probs, states)
+        for p, st, x in zip(probs, states, init):
+            st.copy_(S.to_state(p, x))
+        b.sw_batch_set_threads(threads)
+        b.sw_batch_run()
+        assert b.sw_batch_status() == S.SW_OK
+        got = _read(probs, states)
+        with pytest.raises(S.SweptError):
+            b.sw_batch_set_threads(96)
+    for a, c in zip(ref, got):
+        assert np.array_equal(a, c)
+    torch.cuda.synchronize()
+
+
+def test_compensated_heat_items_against_the_oracle():
+    # FP32 hi/lo heat problems of a batch: within 1e-9 of the initial magnitude of the FP64
+    # oracle after 2,000 steps (their Euler neighbours are covered by the precision tests)
+    import torch
+    items, probs, states, init = _setup(S.SW_FP32_COMP, count=24, seed=13)
+    nsteps = 2000
+    with S.Batch(probs, states, nsteps) as b:
+        b.sw_batch_run()
+        assert b.sw_batch_status() == S.SW_OK
+        got = _read(probs, states)
+    checked = 0
+    for i, it in enumerate(items):
+        if it.scheme != "heat":
+            continue
+        want = oracle.heat_run(it.planes[0], it.r, nsteps)
+        assert np.max(np.abs(got[i].reshape(-1) - want)) <= 1e-9 * np.max(np.abs(it.planes)), i
+        checked += 1
+    assert checked >= 10
+    torch.cuda.synchronize()
+
+
 def test_batch_graph_replay_is_deterministic():
     import torch
     items, probs, states, init = _setup(S.SW_FP32_COMP, count=16, seed=9)
