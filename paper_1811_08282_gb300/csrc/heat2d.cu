@@ -60,6 +60,11 @@ template <> struct Ops2D<float> { using O = OpsF; };
 
 constexpr int kThreads2D = 256;
 
+// ceil(2^32 / w) for every window width w = 1 .. kMagicMax (the row of cell t of a window w
+// wide is umulhi(t, magic[w])); filled from the host at sw2d_create, identical on every device
+constexpr int kMagicMax = 1026;
+__constant__ unsigned c_magic[kMagicMax + 1];
+
 // ------------------------------------------------------------------ per-step
 // V consecutive cells of a row as 16-byte vector accesses (VEC) or scalars.
 template <class T, int V, bool VEC> struct RowIO {
@@ -176,7 +181,7 @@ __device__ __forceinline__ void compute_window(const Frame<T> &f, int64_t lev, i
                                                T ry) {
     using O = typename Ops2D<T>::O;
     const unsigned w = (unsigned)(x1 - x0 + 1), cnt = w * (unsigned)(y1 - y0 + 1);
-    const unsigned m = 0xFFFFFFFFu / w + 1u;  // ceil(2^32 / w), w >= 2
+    const unsigned m = c_magic[w];  // ceil(2^32 / w), w >= 2
     const T *src = f.s + (int)((lev - 1) & 1) * f.slot;
     T *dst = f.s + (int)(lev & 1) * f.slot;
     const int org = (y0 - f.cy + f.H + 1) * f.RS + (x0 - f.cx + f.H + 1);
@@ -550,6 +555,14 @@ int sw2d_create(const sw_heat2d *p, sw_handle2d **out) {
     };
     cudaError_t e = cudaMalloc(&h->plane, size_t(p->nx * p->ny) * h->es);
     if (e != cudaSuccess) return fail(cuda_status2d(e));
+    {   // the row-mapping multipliers (the same values on every device; written once per create)
+        unsigned magic[kMagicMax + 1];
+        magic[0] = 0;
+        magic[1] = 0;  // never used: windows are at least 2 wide
+        for (int w = 2; w <= kMagicMax; ++w) magic[w] = 0xFFFFFFFFu / (unsigned)w + 1u;
+        e = cudaMemcpyToSymbol(c_magic, magic, sizeof(magic));
+        if (e != cudaSuccess) return fail(cuda_status2d(e));
+    }
     if (p->method == SW_SWEPT) {
         h->W = p->tile_width ? p->tile_width : 64;
         h->H = h->W / 2;

@@ -4,6 +4,7 @@
         --method swept --n 16777216 --steps 2048 --width 1024 [--repeat 1] [--generic]
     python -m paper_1811_08282_gb300.profile_case --scheme heat2d --precision fp64 \
         --nx 4096 --ny 4096 --steps 256 --width 64
+    python -m paper_1811_08282_gb300.profile_case --scheme batch --count 1024 --steps 200
 
 Inputs are the seeded synthetic states of ``inputs`` (heat: 32 sine modes;
 Euler: Sod, or 64 random Riemann segments with --init riemann). Prints the
@@ -22,7 +23,8 @@ PREC = {"fp64": S.SW_FP64, "fp32": S.SW_FP32, "fp32_comp": S.SW_FP32_COMP}
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--scheme", choices=("heat", "euler", "heat2d"), default="heat")
+    ap.add_argument("--scheme", choices=("heat", "euler", "heat2d", "batch"), default="heat")
+    ap.add_argument("--count", type=int, default=1024, help="batch: problems (the batched workload's first ones)")
     ap.add_argument("--nx", type=int, default=4096, help="heat2d: grid width")
     ap.add_argument("--ny", type=int, default=4096, help="heat2d: grid height")
     ap.add_argument("--precision", choices=tuple(PREC), default="fp64")
@@ -43,6 +45,8 @@ def main(argv=None):
     build.build()
     if a.scheme == "heat2d":
         return run2d(a)
+    if a.scheme == "batch":
+        return run_batch(a)
     heat = a.scheme == "heat"
     bc = a.boundary or ("periodic" if heat else "transmissive")
     p = S.Problem(scheme=S.SW_HEAT if heat else S.SW_EULER, precision=PREC[a.precision],
@@ -75,6 +79,33 @@ def main(argv=None):
     print(json.dumps({"scheme": a.scheme, "precision": a.precision, "method": a.method, "n": a.n,
                       "steps": a.steps, "width": a.width, "generic": a.generic, "flags": a.flags, "launches": launches, "seconds": t,
                       "gcell_updates_per_s": a.n * a.steps / t / 1e9, "status": rc}))
+    return 0 if rc == 0 else 1
+
+
+def run_batch(a) -> int:
+    """The batched workload's first `count` problems (FP32 hi/lo unless --precision says
+    otherwise) at the widths the tuner usually picks (heat 1024, Euler flattened 256), one
+    persistent launch from its CUDA graph after one untimed run."""
+    import torch
+    from . import batched
+    items = batched.default_items(4096, seed=7)[: a.count]
+    widths = {"heat": (1024, 0), "euler": (256, S.SW_FLAG_FLATTENED)}
+    prec = PREC[a.precision] if a.precision != "fp64" else S.SW_FP32_COMP
+    bt = batched.build(items, a.steps, precision=prec, widths=widths)
+    bt.batch.sw_batch_run()
+    rc = bt.batch.sw_batch_status()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    bt.batch.sw_batch_run()
+    e1.record()
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    rc = rc or bt.batch.sw_batch_status()
+    print(json.dumps({"scheme": "batch", "problems": len(items), "cells": bt.cells, "steps": a.steps,
+                      "items": bt.batch.sw_batch_items(), "seconds": t,
+                      "gcell_steps_per_s": bt.cells * a.steps / t / 1e9, "status": rc}))
+    bt.batch.close()
     return 0 if rc == 0 else 1
 
 
