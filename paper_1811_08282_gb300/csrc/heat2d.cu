@@ -65,6 +65,13 @@ constexpr int kThreads2D = 256;
 constexpr int kMagicMax = 1026;
 __constant__ unsigned c_magic[kMagicMax + 1];
 
+// The quotient and remainder of t by len for the strip loops (t < 8 * len, 2 <= len <=
+// kMagicMax: exact, since t * len < 2^32)
+__device__ __forceinline__ void div_len(int t, int len, int &q, int &r) {
+    q = (int)__umulhi((unsigned)t, c_magic[len]);
+    r = t - q * len;
+}
+
 // ------------------------------------------------------------------ per-step
 // V consecutive cells of a row as 16-byte vector accesses (VEC) or scalars.
 template <class T, int V, bool VEC> struct RowIO {
@@ -201,7 +208,8 @@ __device__ __forceinline__ void export_pyramid(const Frame<T> &f, int64_t lev, i
                                                T *sx, T *sy, int tile, int i, int H, int W) {
     const int len = x1 - x0 + 1;  // square window
     for (int t = threadIdx.x; t < 8 * len; t += blockDim.x) {
-        const int q = t / len, r = t - q * len;  // q: which of the 8 edge lines
+        int q, r;  // q: which of the 8 edge lines
+        div_len(t, len, q, r);
         const int side = (q >> 1) & 1, k = q & 1;
         if (q < 4) {  // x-strips
             const int x = side == 0 ? x0 + k : x1 - 1 + k;
@@ -263,7 +271,8 @@ __global__ void __launch_bounds__(kThreads2D) k2d_bridges(Swept2DArgs<T> a) {
         const int len = W - 2 * (i - 1);
         const T *src = xb ? a.pin_x : a.pin_y;
         for (int t = threadIdx.x; t < 4 * len; t += blockDim.x) {
-            const int q = t / len, r = t - q * len;  // q: (neighbour, k)
+            int q, r;  // q: (neighbour, k)
+            div_len(t, len, q, r);
             const int k = q & 1, hiside = q >> 1;
             // the low-side pyramid exports its high side (1), the high-side pyramid its low side (0)
             const T v = src[strip_off(hiside ? thi : tlo, hiside ? 0 : 1, i - 1, k, H, W) + r];
@@ -293,7 +302,8 @@ __global__ void __launch_bounds__(kThreads2D) k2d_bridges(Swept2DArgs<T> a) {
         const int len = 2 * i;
         T *dst = xb ? a.brx : a.bry;
         for (int t = threadIdx.x; t < 4 * len; t += blockDim.x) {
-            const int q = t / len, r = t - q * len;
+            int q, r;
+            div_len(t, len, q, r);
             const int k = q & 1, side = q >> 1;
             T v;
             if (xb) v = f.at(base + i, x0 + r, side == 0 ? y0 + k : y1 - 1 + k);
@@ -322,7 +332,8 @@ __global__ void __launch_bounds__(kThreads2D) k2d_octa(Swept2DArgs<T> a) {
         const int len = 2 * (i - 1);  // the bridges' strips at step i - 1
         if (len > 0) {
             for (int t = threadIdx.x; t < 8 * len; t += blockDim.x) {
-                const int q = t / len, r = t - q * len;
+                int q, r;
+                div_len(t, len, q, r);
                 const int k = q & 1, which = q >> 1;
                 // 0: y-bridge on the left (its right columns), 1: on the right (its left columns),
                 // 2: x-bridge below (its top rows), 3: above (its bottom rows)
