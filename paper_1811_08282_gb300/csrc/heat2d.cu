@@ -58,7 +58,14 @@ template <class T> struct Ops2D;
 template <> struct Ops2D<double> { using O = OpsD; };
 template <> struct Ops2D<float> { using O = OpsF; };
 
-constexpr int kThreads2D = 256;
+constexpr int kThreads2D = 256;       // per-step kernel; swept kernels at W < 128
+constexpr int kThreads2DWide = 1024;  // swept kernels at W >= 128: one CTA per SM fits the frame
+
+// Threads of a swept CTA: the frame of W >= 128 leaves room for one CTA per SM, which then
+// takes all the warps it can. The kernels are instantiated for both counts, each with a
+// launch bound that keeps the narrow form at its resident-CTA count (FP32: 6 per SM,
+// FP64: 3, what the frame's shared memory allows at W = 64).
+__host__ __device__ constexpr int swept_threads2d(int W) { return W >= 128 ? kThreads2DWide : kThreads2D; }
 
 // ceil(2^32 / w) for every window width w = 1 .. kMagicMax (the row of cell t of a window w
 // wide is umulhi(t, magic[w])); filled from the host at sw2d_create, identical on every device
@@ -235,8 +242,8 @@ __device__ void pyramid_part(const Frame<T> &f, const Swept2DArgs<T> &a, int64_t
 }
 
 // Up: the pyramids of phase 0 from the state (level 0)
-template <class T>
-__global__ void __launch_bounds__(kThreads2D) k2d_up(Swept2DArgs<T> a) {
+template <class T, int NT>
+__global__ void __launch_bounds__(NT, NT == kThreads2D ? (sizeof(T) == 4 ? 6 : 3) : 1) k2d_up(Swept2DArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int bx = blockIdx.x % a.Mx, by = blockIdx.x / a.Mx;
     const int RS = a.W + 3, H = a.H;
@@ -250,8 +257,8 @@ __global__ void __launch_bounds__(kThreads2D) k2d_up(Swept2DArgs<T> a) {
 }
 
 // Bridges of phase p: blockIdx.y = 0 x-bridges (lower in x, upper in y), 1 y-bridges.
-template <class T>
-__global__ void __launch_bounds__(kThreads2D) k2d_bridges(Swept2DArgs<T> a) {
+template <class T, int NT>
+__global__ void __launch_bounds__(NT, NT == kThreads2D ? (sizeof(T) == 4 ? 6 : 3) : 1) k2d_bridges(Swept2DArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int b0 = blockIdx.x % a.Mx, b1 = blockIdx.x / a.Mx;  // (x index, y index)
     const int W = a.W, H = a.H, RS = W + 3;
@@ -315,8 +322,8 @@ __global__ void __launch_bounds__(kThreads2D) k2d_bridges(Swept2DArgs<T> a) {
 
 // Octahedra of phase p: the lower part (lower x lower) up to the full tile at F, then the
 // pyramid of phase p (or, in the last phase, the tile stored to the state).
-template <class T>
-__global__ void __launch_bounds__(kThreads2D) k2d_octa(Swept2DArgs<T> a) {
+template <class T, int NT>
+__global__ void __launch_bounds__(NT, NT == kThreads2D ? (sizeof(T) == 4 ? 6 : 3) : 1) k2d_octa(Swept2DArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int bx = blockIdx.x % a.Mx, by = blockIdx.x / a.Mx;
     const int W = a.W, H = a.H, RS = W + 3;
@@ -514,6 +521,7 @@ template <class T> int run2d(sw_handle2d *h, void *state_v, int64_t nsteps, cuda
             a.brx = reinterpret_cast<T *>(h->brx);
             a.bry = reinterpret_cast<T *>(h->bry);
             const unsigned tiles = (unsigned)(h->Mx * h->My);
+            const int nt = swept_threads2d(h->W);
             for (int64_t p = 0; p <= P; ++p) {
                 a.p = (int)(p & 1) ? 1 : 2;  // only the parity of p matters to the kernels
                 if (p == 0) a.p = 0;
@@ -525,15 +533,18 @@ template <class T> int run2d(sw_handle2d *h, void *state_v, int64_t nsteps, cuda
                 a.pout_y = reinterpret_cast<T *>(h->pyry[p & 1]);
                 if (p == 0) {
                     trace2d_begin(h, launches, 0, st);
-                    k2d_up<T><<<tiles, kThreads2D, h->smem, st>>>(a);
+                    if (nt == kThreads2D) k2d_up<T, kThreads2D><<<tiles, nt, h->smem, st>>>(a);
+                    else k2d_up<T, kThreads2DWide><<<tiles, nt, h->smem, st>>>(a);
                     trace2d_end(h, launches++, st);
                     continue;
                 }
                 trace2d_begin(h, launches, 1, st);
-                k2d_bridges<T><<<dim3(tiles, 2), kThreads2D, h->smem, st>>>(a);
+                if (nt == kThreads2D) k2d_bridges<T, kThreads2D><<<dim3(tiles, 2), nt, h->smem, st>>>(a);
+                else k2d_bridges<T, kThreads2DWide><<<dim3(tiles, 2), nt, h->smem, st>>>(a);
                 trace2d_end(h, launches++, st);
                 trace2d_begin(h, launches, p == P ? 4 : 2, st);
-                k2d_octa<T><<<tiles, kThreads2D, h->smem, st>>>(a);
+                if (nt == kThreads2D) k2d_octa<T, kThreads2D><<<tiles, nt, h->smem, st>>>(a);
+                else k2d_octa<T, kThreads2DWide><<<tiles, nt, h->smem, st>>>(a);
                 trace2d_end(h, launches++, st);
             }
         }
@@ -581,15 +592,21 @@ int sw2d_create(const sw_heat2d *p, sw_handle2d **out) {
         h->My = (int)(p->ny / h->W);
         if (h->W > max_width2d(h->es)) return fail(SW_ERR_UNSUPPORTED);
         h->smem = smem2d(h->W, h->es);
-        const void *fns[3];
+        const void *fns[6];
         if (p->precision == SW_FP64) {
-            fns[0] = (const void *)k2d_up<double>;
-            fns[1] = (const void *)k2d_bridges<double>;
-            fns[2] = (const void *)k2d_octa<double>;
+            fns[0] = (const void *)k2d_up<double, kThreads2D>;
+            fns[1] = (const void *)k2d_bridges<double, kThreads2D>;
+            fns[2] = (const void *)k2d_octa<double, kThreads2D>;
+            fns[3] = (const void *)k2d_up<double, kThreads2DWide>;
+            fns[4] = (const void *)k2d_bridges<double, kThreads2DWide>;
+            fns[5] = (const void *)k2d_octa<double, kThreads2DWide>;
         } else {
-            fns[0] = (const void *)k2d_up<float>;
-            fns[1] = (const void *)k2d_bridges<float>;
-            fns[2] = (const void *)k2d_octa<float>;
+            fns[0] = (const void *)k2d_up<float, kThreads2D>;
+            fns[1] = (const void *)k2d_bridges<float, kThreads2D>;
+            fns[2] = (const void *)k2d_octa<float, kThreads2D>;
+            fns[3] = (const void *)k2d_up<float, kThreads2DWide>;
+            fns[4] = (const void *)k2d_bridges<float, kThreads2DWide>;
+            fns[5] = (const void *)k2d_octa<float, kThreads2DWide>;
         }
         for (const void *fn : fns) {
             e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
