@@ -14,7 +14,7 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    # GPU tests are skipped (not failed) on a machine without a GPU; on a GPU machine
+    # GPU tests are skipped (not failed) on a machine without a GPU; on a machine with one
     # they run and a missing native library fails loudly inside the tests.
     try:
         import torch
