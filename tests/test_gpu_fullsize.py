@@ -171,3 +171,30 @@ def test_large_grid_fp32_swept_equals_perstep():
     sw = run_gpu(_heat(n, 1024, 0.3, S.SW_FP32), u0[None], steps)
     ps = run_gpu(_heat(n, 1024, 0.3, S.SW_FP32, S.SW_PERSTEP), u0[None], steps)
     assert np.array_equal(sw, ps)
+
+
+@pytest.mark.parametrize("prec", [S.SW_FP64, S.SW_FP32])
+def test_heat2d_8192_squared_2048_steps(prec):
+    # the benchmark's 2D workload in its launch configuration (W = 64): swept == per-step bitwise
+    # and the exact mode solution of the oracle at sampled cells (relative to the initial maximum)
+    import torch
+    n, steps, r = 8192, 2048, 0.2
+    m = I.heat2d_modes(n, n, 16, seed=6, kmax=16)
+    u0 = I.heat2d_initial(m)
+    dt = torch.float64 if prec == S.SW_FP64 else torch.float32
+    outs = []
+    for method in (S.SW_SWEPT, S.SW_PERSTEP):
+        p = S.Heat2D(precision=prec, method=method, tile_width=64 if method == S.SW_SWEPT else 0, nx=n, ny=n,
+                     rx=r, ry=r)
+        st = torch.as_tensor(u0.reshape(-1), device="cuda").to(dt).clone()
+        with S.Handle2D(p) as h:
+            h.sw2d_run(st, steps)
+        outs.append(st)
+    assert torch.equal(outs[0], outs[1])
+    rng = np.random.default_rng(11)
+    ii, jj = rng.integers(0, n, 4096), rng.integers(0, n, 4096)
+    want = oracle.heat2d_modes(n, n, r, r, steps, m.amps, m.kx, m.ky, m.fx, m.fy, ii, jj)
+    got = outs[0].double().cpu().numpy().reshape(n, n)[jj, ii]
+    err = np.max(np.abs(got - want)) / np.max(np.abs(u0))
+    assert err <= (1e-12 if prec == S.SW_FP64 else 1e-5), err
+    torch.cuda.synchronize()
