@@ -48,8 +48,9 @@ extern "C" {
  * 3: swept Euler runs default to the flattened form where W allows it;
  * SW_FLAG_LENGTHENED selects the lengthened form for swept runs too; sw_autotune
  * also picks the Euler form.
- * 4: the two-dimensional heat entry points sw2d_*; sw_batch_set_threads. */
-#define SW_ABI_VERSION 4
+ * 4: the two-dimensional heat entry points sw2d_*; sw_batch_set_threads.
+ * 5: sw2d_set_threads / sw2d_threads. */
+#define SW_ABI_VERSION 5
 
 #if defined(__GNUC__)
 #define SW_API __attribute__((visibility("default")))
@@ -371,6 +372,15 @@ SW_API int sw2d_run(sw_handle2d *h, void *state, int64_t nsteps, void *stream);
 /* Launches issued by the last sw2d_run, and the tile width in use. */
 SW_API int64_t sw2d_last_launch_count(const sw_handle2d *h);
 SW_API int32_t sw2d_tile_width(const sw_handle2d *h);
+/* Threads per CTA of the swept kernels of a swept handle: `threads` for the Up and
+ * octahedra launches, `bridge_threads` for the bridges; each 128, 256 or 1024, 0 for the
+ * default (256 below W = 128, 1024 from there). A tuning choice only: every count
+ * computes the same cells with the same arithmetic, so results are bitwise equal.
+ * Takes effect at the next sw2d_run. SW_ERR_BAD_ARG for another count or a per-step
+ * handle. sw2d_threads returns the count in use (bridges != 0: the bridges'), 0 for a
+ * per-step handle. */
+SW_API int sw2d_set_threads(sw_handle2d *h, int32_t threads, int32_t bridge_threads);
+SW_API int32_t sw2d_threads(const sw_handle2d *h, int32_t bridges);
 /* Tracing, as sw_set_timing / sw_launch_times (kinds: 0 Up pyramids, 1 bridges,
  * 2 octahedra, 3 per-step, 4 the last phase's octahedra). */
 SW_API int sw2d_set_timing(sw_handle2d *h, int64_t capacity);

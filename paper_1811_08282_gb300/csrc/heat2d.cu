@@ -61,23 +61,29 @@ template <> struct Ops2D<float> { using O = OpsF; };
 constexpr int kThreads2D = 256;       // per-step kernel; swept kernels at W < 128
 constexpr int kThreads2DWide = 1024;  // swept kernels at W >= 128: one CTA per SM fits the frame
 
-// Threads of a swept CTA: the frame of W >= 128 leaves room for one CTA per SM, which then
-// takes all the warps it can. The kernels are instantiated for both counts, each with a
-// launch bound that keeps the narrow form at its resident-CTA count (FP32: 6 per SM,
-// FP64: 3, what the frame's shared memory allows at W = 64).
+// Threads of a swept CTA by default: the frame of W >= 128 leaves room for one CTA per SM,
+// which then takes all the warps it can. The swept kernels are instantiated for 128, 256
+// and 1024 threads (sw2d_set_threads), each with a launch bound that keeps the resident-CTA
+// count the frame's shared memory allows at W = 64 (FP32: 6 per SM, FP64: 3; one at 1024).
 __host__ __device__ constexpr int swept_threads2d(int W) { return W >= 128 ? kThreads2DWide : kThreads2D; }
+template <class T, int NT> constexpr int min_ctas2d() { return NT >= kThreads2DWide ? 1 : (sizeof(T) == 4 ? 6 : 3); }
 
-// ceil(2^32 / w) for every window width w = 1 .. kMagicMax (the row of cell t of a window w
-// wide is umulhi(t, magic[w])); filled from the host at sw2d_create, identical on every device
+// Swept kernels compiled for one tile width WC (0: W read from the arguments). With W a
+// constant, the frame's row stride, the slot size and the strip offsets are immediates, which
+// takes the shared-memory address arithmetic out of the FP32 walker's inner loop (FP32 is
+// bound by instruction issue; FP64 by its pipe, so it keeps the generic form). Instantiated
+// for FP32 at W = 32 and 64 with 128 or 256 threads, and W = 128 with 256 or 1024.
+template <class T, int NT, int WC> constexpr bool specialised2d() {
+    return sizeof(T) == 4 && (((WC == 32 || WC == 64) && (NT == 128 || NT == kThreads2D)) ||
+                              (WC == 128 && (NT == kThreads2D || NT == kThreads2DWide)));
+}
+
+// ceil(2^32 / w) for w = 2 .. kMagicMax: umulhi(t, magic[w]) = t / w while t * w < 2^32 (the
+// band and column of a window's walker, the line of a strip element); filled from the host at
+// sw2d_create, identical on every device
 constexpr int kMagicMax = 1026;
 __constant__ unsigned c_magic[kMagicMax + 1];
 
-// The quotient and remainder of t by len for the strip loops (t < 8 * len, 2 <= len <=
-// kMagicMax: exact, since t * len < 2^32)
-__device__ __forceinline__ void div_len(int t, int len, int &q, int &r) {
-    q = (int)__umulhi((unsigned)t, c_magic[len]);
-    r = t - q * len;
-}
 
 // ------------------------------------------------------------------ per-step
 // V consecutive cells of a row as 16-byte vector accesses (VEC) or scalars.
@@ -171,228 +177,266 @@ __device__ __forceinline__ void nbrs(int p, int b, int M, int &lo, int &hi) {
     }
 }
 
-// strip element (tile, side, step, k, r): one buffer holds 2 sides x H steps x 2 x W per tile
-__device__ __forceinline__ int64_t strip_off(int tile, int side, int i, int k, int H, int W) {
-    return ((((int64_t)tile * 2 + side) * H + i) * 2 + k) * W;
+// Strips: one buffer holds, per tile, 2 sides x H steps x 2 lines x W values; element
+// (tile, side, step i, line k, r) sits at ((tile * 2 + side) * H + i) * 2W + k * W + r. A
+// kernel forms the 64-bit base of each strip block it touches once and indexes the rest
+// (below 4 * H * W) in 32 bits.
+template <class T> __device__ __forceinline__ T *strip_block(T *buf, int tile, int side, int H, int W) {
+    return buf + ((int64_t)tile * 2 + side) * H * 2 * W;
 }
+__device__ __forceinline__ int strip_at(int i, int k, int W) { return (i * 2 + k) * W; }
 
-// The shared frame of a region centred at (cx, cy): position (x, y) absolute (unwrapped)
-// -> (x - cx + H + 1, y - cy + H + 1).
+// The shared frame of a region centred at (cx, cy), in local coordinates: the absolute
+// (unwrapped) position (x, y) is (X, Y) = (x - cx + H + 1, y - cy + H + 1), 0 <= X, Y <= W + 1.
+// Window bounds at step i in local coordinates: upper (narrowing) [i + 1, W - i], lower
+// (widening) [H + 1 - i, H + i].
 template <class T> struct Frame {
     T *s;
-    int RS, slot, cx, cy, H;
-    __device__ __forceinline__ T &at(int64_t lev, int x, int y) const {
-        return s[(int)(lev & 1) * slot + (y - cy + H + 1) * RS + (x - cx + H + 1)];
-    }
+    int RS, slot;
+    __device__ __forceinline__ T &at(int64_t lev, int X, int Y) const { return s[((int)lev & 1) * slot + Y * RS + X]; }
 };
 
-// compute the window [x0, x1] x [y0, y1] at level lev from lev - 1: the block's threads
-// run over the window's cells in row-major order (consecutive threads on consecutive
-// cells of a row), so narrow windows keep every lane busy; the row of cell t is
-// umulhi(t, ceil(2^32 / w)), exact while t * w < 2^32 (t < w * h <= 2^16 here).
-template <class T>
-__device__ __forceinline__ void compute_window(const Frame<T> &f, int64_t lev, int x0, int x1, int y0, int y1, T rx,
-                                               T ry) {
-    using O = typename Ops2D<T>::O;
-    const unsigned w = (unsigned)(x1 - x0 + 1), cnt = w * (unsigned)(y1 - y0 + 1);
-    const unsigned m = c_magic[w];  // ceil(2^32 / w), w >= 2
-    const T *src = f.s + (int)((lev - 1) & 1) * f.slot;
-    T *dst = f.s + (int)(lev & 1) * f.slot;
-    const int org = (y0 - f.cy + f.H + 1) * f.RS + (x0 - f.cx + f.H + 1);
-    // a thread's cells are independent: unrolled, their shared-memory loads overlap
-#pragma unroll 4
-    for (unsigned t = threadIdx.x; t < cnt; t += blockDim.x) {
-        const unsigned yy = __umulhi(t, m), xx = t - yy * w;
-        const int q = org + (int)yy * f.RS + (int)xx;
-        dst[q] = heat2d_update<O>(rx, ry, src[q - 1], src[q + 1], src[q], src[q - f.RS], src[q + f.RS]);
+// `LINES` strip lines of `len` elements each over a block of NT threads, packed: element t
+// of the block's LINES * len is (line t / len, entry t % len), so consecutive threads take
+// consecutive entries across line ends and short lines leave no lane idle (measured ahead of
+// one line per warp in FP32, where issue slots bind). t * len < 2^32: t < 8 * (W + 2).
+template <int NT, int LINES, class Fn> __device__ __forceinline__ void over_lines(int len, Fn &&fn) {
+    const unsigned m = c_magic[len];  // len >= 2 whenever the loop runs
+    for (int t = (int)threadIdx.x; t < LINES * len; t += NT) {
+        const int q = (int)__umulhi((unsigned)t, m), r = t - q * len;
+        fn(q, r);
     }
 }
 
-// export the 2-deep edges of a pyramid window (x-strips: columns x0, x0+1 / x1-1, x1 over
-// rows y0..y1; y-strips: rows over columns) at step i
-template <class T>
-__device__ __forceinline__ void export_pyramid(const Frame<T> &f, int64_t lev, int x0, int x1, int y0, int y1,
-                                               T *sx, T *sy, int tile, int i, int H, int W) {
-    const int len = x1 - x0 + 1;  // square window
-    for (int t = threadIdx.x; t < 8 * len; t += blockDim.x) {
-        int q, r;  // q: which of the 8 edge lines
-        div_len(t, len, q, r);
-        const int side = (q >> 1) & 1, k = q & 1;
-        if (q < 4) {  // x-strips
-            const int x = side == 0 ? x0 + k : x1 - 1 + k;
-            sx[strip_off(tile, side, i, k, H, W) + r] = f.at(lev, x, y0 + r);
-        } else {
-            const int y = side == 0 ? y0 + k : y1 - 1 + k;
-            sy[strip_off(tile, side, i, k, H, W) + r] = f.at(lev, x0 + r, y);
+__device__ __forceinline__ int64_t wrap(int64_t x, int64_t n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
+// compute the window [X0, X1] x [Y0, Y1] (local) at level lev from lev - 1 with a block of
+// NT threads. The quotients come from the constant table (t * w < 2^32 throughout: t < (W +
+// 2)^2 <= 120^2 for FP64, t < NT for FP32).
+//  FP64 (bound by the FP64 pipe, which is paid per warp instruction): the threads run over
+//    the window's cells in row-major order, consecutive threads on consecutive cells, so
+//    every warp instruction but the last of a level has all 32 lanes busy.
+//  FP32 (bound by instruction issue): each thread walks down one column over a band of
+//    consecutive rows: nb = min(h, floor(NT / w)) bands of ceil(h / nb) rows per column,
+//    consecutive threads on consecutive columns (a warp's shared-memory accesses are
+//    consecutive). The walker carries the cell above and the cell itself in registers, so
+//    a cell costs three shared loads (left, right, below) and one store, and the row
+//    mapping is paid once per band instead of once per cell; four rows are loaded before
+//    any of them is stored.
+template <int NT, class T>
+__device__ __forceinline__ void compute_window(const Frame<T> &f, int64_t lev, int X0, int X1, int Y0, int Y1, T rx,
+                                               T ry) {
+    using O = typename Ops2D<T>::O;
+    const int RS = f.RS;
+    const T *src = f.s + (((int)lev - 1) & 1) * f.slot;
+    T *dst = f.s + ((int)lev & 1) * f.slot;
+    const unsigned w = (unsigned)(X1 - X0 + 1), h = (unsigned)(Y1 - Y0 + 1);  // both >= 2
+    if constexpr (sizeof(T) == 8) {
+        const unsigned cnt = w * h, m = c_magic[w];
+        const int org = Y0 * RS + X0;
+#pragma unroll 4
+        // the stride is read from blockDim, not the compile-time NT: with a constant stride
+        // the unrolled loop ran 7 % slower (FP64, W = 64, 8192^2), the same cells in the same order
+        for (unsigned t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const unsigned yy = __umulhi(t, m), xx = t - yy * w;
+            const int q = org + (int)yy * RS + (int)xx;
+            dst[q] = heat2d_update<O>(rx, ry, src[q - 1], src[q + 1], src[q], src[q - RS], src[q + RS]);
+        }
+    } else {
+        const unsigned nb = min(max(__umulhi(NT, c_magic[w]), 1u), h);
+        const unsigned L = nb == 1 ? h : __umulhi(h + nb - 1, c_magic[nb]);
+        const unsigned t = threadIdx.x;
+        if (t >= w * nb) return;
+        const unsigned band = __umulhi(t, c_magic[w]), col = t - band * w;
+        const unsigned ya = band * L;
+        if (ya >= h) return;
+        const int rows = (int)(min(h, ya + L) - ya);
+        int q = (Y0 + (int)ya) * RS + X0 + (int)col;
+        T up = src[q - RS], c = src[q];
+        int y = 0;
+        for (; y + 4 <= rows; y += 4) {
+            T l[4], r[4], d[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                l[k] = src[q + k * RS - 1];
+                r[k] = src[q + k * RS + 1];
+                d[k] = src[q + (k + 1) * RS];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                dst[q + k * RS] = heat2d_update<O>(rx, ry, l[k], r[k], c, up, d[k]);
+                up = c;
+                c = d[k];
+            }
+            q += 4 * RS;
+        }
+        for (; y < rows; ++y) {
+            const T dn = src[q + RS];
+            dst[q] = heat2d_update<O>(rx, ry, src[q - 1], src[q + 1], c, up, dn);
+            up = c;
+            c = dn;
+            q += RS;
         }
     }
 }
 
-// The upper part of a structure of phase q (the pyramid): steps 0..H-1 from the full
-// tile at level F (already in the frame), exporting both kinds of strips per step.
-template <class T>
-__device__ void pyramid_part(const Frame<T> &f, const Swept2DArgs<T> &a, int64_t F, int tile, T *sx, T *sy) {
-    const int H = a.H, cx = f.cx, cy = f.cy;
-    export_pyramid(f, F, cx - H, cx + H - 1, cy - H, cy + H - 1, sx, sy, tile, 0, H, a.W);
+// export the 2-deep edges of the pyramid window at step i, [i + 1, W - i]^2 (local): line q
+// < 4 is an x-strip (columns i+1+k / W-i-1+k over the window's rows), q >= 4 a y-strip (rows
+// over its columns); side = (q >> 1) & 1, k = q & 1. sxb / syb: this tile's strip blocks.
+template <int NT, class T>
+__device__ __forceinline__ void export_pyramid(const Frame<T> &f, int64_t lev, int i, int H, int W, T *sxb,
+                                               T *syb) {
+    over_lines<NT, 8>(W - 2 * i, [&](int q, int r) {
+        const int side = (q >> 1) & 1, k = q & 1;
+        const int edge = side == 0 ? i + 1 + k : W - i - 1 + k;
+        const int off = strip_at(side * H + i, k, W) + r;
+        if (q < 4) sxb[off] = f.at(lev, edge, i + 1 + r);
+        else syb[off] = f.at(lev, i + 1 + r, edge);
+    });
+}
+
+// The upper part of a structure (the pyramid): steps 0..H-1 from the full tile at level F
+// (already in the frame), exporting both kinds of strips per step.
+template <int NT, class T>
+__device__ void pyramid_part(const Frame<T> &f, const Swept2DArgs<T> &a, int W, int H, int64_t F, int tile, T *sx,
+                             T *sy) {
+    T *sxb = strip_block(sx, tile, 0, H, W), *syb = strip_block(sy, tile, 0, H, W);
+    export_pyramid<NT>(f, F, 0, H, W, sxb, syb);
     for (int i = 1; i < H; ++i) {
-        compute_window(f, F + i, cx - H + i, cx + H - 1 - i, cy - H + i, cy + H - 1 - i, a.rx, a.ry);
+        compute_window<NT>(f, F + i, i + 1, W - i, i + 1, W - i, a.rx, a.ry);
         __syncthreads();
-        export_pyramid(f, F + i, cx - H + i, cx + H - 1 - i, cy - H + i, cy + H - 1 - i, sx, sy, tile, i, H, a.W);
+        export_pyramid<NT>(f, F + i, i, H, W, sxb, syb);
     }
 }
 
-// Up: the pyramids of phase 0 from the state (level 0)
-template <class T, int NT>
-__global__ void __launch_bounds__(NT, NT == kThreads2D ? (sizeof(T) == 4 ? 6 : 3) : 1) k2d_up(Swept2DArgs<T> a) {
+// Up: the pyramids of phase 0 from the state (level 0); a warp per row of the tile
+template <class T, int NT, int WC>
+__global__ void __launch_bounds__(NT, (min_ctas2d<T, NT>())) k2d_up(Swept2DArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int bx = blockIdx.x % a.Mx, by = blockIdx.x / a.Mx;
-    const int RS = a.W + 3, H = a.H;
-    Frame<T> f{reinterpret_cast<T *>(smem_raw), RS, (a.W + 2) * RS, centre2d(0, bx, a.W), centre2d(0, by, a.W), H};
-    for (int t = threadIdx.x; t < a.W * a.W; t += blockDim.x) {
-        const int y = f.cy - H + t / a.W, x = f.cx - H + t % a.W;
-        f.at(0, x, y) = a.state[(int64_t)((y + a.ny) % a.ny) * a.nx + (x + a.nx) % a.nx];
+    const int W = WC ? WC : a.W, H = W / 2;
+    const Frame<T> f{reinterpret_cast<T *>(smem_raw), W + 3, (W + 2) * (W + 3)};
+    const int64_t gx0 = (int64_t)centre2d(0, bx, W) - H, gy0 = (int64_t)centre2d(0, by, W) - H;
+    for (int Y = 1 + (int)(threadIdx.x >> 5); Y <= W; Y += NT / 32) {
+        const T *row = a.state + wrap(gy0 + Y - 1, a.ny) * a.nx;
+        for (int X = 1 + (int)(threadIdx.x & 31); X <= W; X += 32) f.at(0, X, Y) = row[wrap(gx0 + X - 1, a.nx)];
     }
     __syncthreads();
-    pyramid_part(f, a, 0, blockIdx.x, a.pout_x, a.pout_y);
+    pyramid_part<NT>(f, a, W, H, 0, blockIdx.x, a.pout_x, a.pout_y);
 }
 
 // Bridges of phase p: blockIdx.y = 0 x-bridges (lower in x, upper in y), 1 y-bridges.
-template <class T, int NT>
-__global__ void __launch_bounds__(NT, NT == kThreads2D ? (sizeof(T) == 4 ? 6 : 3) : 1) k2d_bridges(Swept2DArgs<T> a) {
+template <class T, int NT, int WC>
+__global__ void __launch_bounds__(NT, (min_ctas2d<T, NT>())) k2d_bridges(Swept2DArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int b0 = blockIdx.x % a.Mx, b1 = blockIdx.x / a.Mx;  // (x index, y index)
-    const int W = a.W, H = a.H, RS = W + 3;
+    const int W = WC ? WC : a.W, H = W / 2;
     const bool xb = blockIdx.y == 0;
-    // x-bridge: centre (c_p(b0), c_{p-1}(b1)); y-bridge: (c_{p-1}(b0), c_p(b1))
-    const int cx = centre2d(xb ? a.p : a.p - 1, b0, W), cy = centre2d(xb ? a.p - 1 : a.p, b1, W);
-    Frame<T> f{reinterpret_cast<T *>(smem_raw), RS, (W + 2) * RS, cx, cy, H};
+    const Frame<T> f{reinterpret_cast<T *>(smem_raw), W + 3, (W + 2) * (W + 3)};
     int lo, hi;  // the two pyramids it imports from (phase p - 1 indices along its lower direction)
     nbrs(a.p, xb ? b0 : b1, xb ? a.Mx : a.My, lo, hi);
     const int tlo = xb ? b1 * a.Mx + lo : lo * a.Mx + b0;
     const int thi = xb ? b1 * a.Mx + hi : hi * a.Mx + b0;
-    const int tile = blockIdx.x;
+    // the low-side pyramid exports its high side (1), the high-side pyramid its low side (0)
+    const T *src = xb ? a.pin_x : a.pin_y;
+    const T *plo = strip_block(src, tlo, 1, H, W), *phi = strip_block(src, thi, 0, H, W);
+    T *dst = strip_block(xb ? a.brx : a.bry, blockIdx.x, 0, H, W);
     const int64_t base = a.F - H;  // level of step 0
     // step i's inputs at level base + i - 1: the pyramids' strips at step i - 1, all of
-    // their W - 2(i-1) entries (rows for an x-bridge, columns for a y-bridge)
+    // their W - 2(i-1) entries (rows i + r for an x-bridge, columns for a y-bridge); line q:
+    // k = q & 1, high-side neighbour q >> 1
     auto inject = [&](int i) {
-        const int len = W - 2 * (i - 1);
-        const T *src = xb ? a.pin_x : a.pin_y;
-        for (int t = threadIdx.x; t < 4 * len; t += blockDim.x) {
-            int q, r;  // q: (neighbour, k)
-            div_len(t, len, q, r);
+        over_lines<NT, 4>(W - 2 * (i - 1), [&](int q, int r) {
             const int k = q & 1, hiside = q >> 1;
-            // the low-side pyramid exports its high side (1), the high-side pyramid its low side (0)
-            const T v = src[strip_off(hiside ? thi : tlo, hiside ? 0 : 1, i - 1, k, H, W) + r];
-            if (xb) {
-                const int x = hiside ? cx + i - 1 + k : cx - i - 1 + k;
-                f.at(base + i - 1, x, cy - H + i - 1 + r) = v;
-            } else {
-                const int y = hiside ? cy + i - 1 + k : cy - i - 1 + k;
-                f.at(base + i - 1, cx - H + i - 1 + r, y) = v;
-            }
-        }
+            const T v = (hiside ? phi : plo)[strip_at(i - 1, k, W) + r];
+            const int across = hiside ? H + i + k : H - i + k;
+            if (xb) f.at(base + i - 1, across, i + r) = v;
+            else f.at(base + i - 1, i + r, across) = v;
+        });
     };
     inject(1);
     __syncthreads();
     for (int i = 1; i < H; ++i) {
-        int x0, x1, y0, y1;
-        if (xb) {
-            x0 = cx - i; x1 = cx + i - 1; y0 = cy - H + i; y1 = cy + H - 1 - i;
-        } else {
-            x0 = cx - H + i; x1 = cx + H - 1 - i; y0 = cy - i; y1 = cy + i - 1;
-        }
-        compute_window(f, base + i, x0, x1, y0, y1, a.rx, a.ry);
+        // the widening direction's window [H + 1 - i, H + i], the narrowing one's [i + 1, W - i]
+        if (xb) compute_window<NT>(f, base + i, H + 1 - i, H + i, i + 1, W - i, a.rx, a.ry);
+        else compute_window<NT>(f, base + i, i + 1, W - i, H + 1 - i, H + i, a.rx, a.ry);
         if (i + 1 < H) inject(i + 1);  // other positions of the slot being written
         __syncthreads();
         // export the edges along the widening direction's normal: an x-bridge its bottom and
-        // top two rows (2i columns), a y-bridge its left and right two columns (2i rows)
-        const int len = 2 * i;
-        T *dst = xb ? a.brx : a.bry;
-        for (int t = threadIdx.x; t < 4 * len; t += blockDim.x) {
-            int q, r;
-            div_len(t, len, q, r);
+        // top two rows (2i columns), a y-bridge its left and right two columns (2i rows);
+        // line q: k = q & 1, side q >> 1
+        over_lines<NT, 4>(2 * i, [&](int q, int r) {
             const int k = q & 1, side = q >> 1;
-            T v;
-            if (xb) v = f.at(base + i, x0 + r, side == 0 ? y0 + k : y1 - 1 + k);
-            else v = f.at(base + i, side == 0 ? x0 + k : x1 - 1 + k, y0 + r);
-            dst[strip_off(tile, side, i, k, H, W) + r] = v;
-        }
+            const int edge = side == 0 ? i + 1 + k : W - i - 1 + k;
+            const T v = xb ? f.at(base + i, H + 1 - i + r, edge) : f.at(base + i, edge, H + 1 - i + r);
+            dst[strip_at(side * H + i, k, W) + r] = v;
+        });
     }
 }
 
 // Octahedra of phase p: the lower part (lower x lower) up to the full tile at F, then the
 // pyramid of phase p (or, in the last phase, the tile stored to the state).
-template <class T, int NT>
-__global__ void __launch_bounds__(NT, NT == kThreads2D ? (sizeof(T) == 4 ? 6 : 3) : 1) k2d_octa(Swept2DArgs<T> a) {
+template <class T, int NT, int WC>
+__global__ void __launch_bounds__(NT, (min_ctas2d<T, NT>())) k2d_octa(Swept2DArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int bx = blockIdx.x % a.Mx, by = blockIdx.x / a.Mx;
-    const int W = a.W, H = a.H, RS = W + 3;
-    const int cx = centre2d(a.p, bx, W), cy = centre2d(a.p, by, W);
-    Frame<T> f{reinterpret_cast<T *>(smem_raw), RS, (W + 2) * RS, cx, cy, H};
+    const int W = WC ? WC : a.W, H = W / 2;
+    const Frame<T> f{reinterpret_cast<T *>(smem_raw), W + 3, (W + 2) * (W + 3)};
     int lx, rx, lb, rt;
     nbrs(a.p, bx, a.Mx, lx, rx);
     nbrs(a.p, by, a.My, lb, rt);
+    // the bridges' strips it imports: the y-bridges left (their right side) and right (their
+    // left side), the x-bridges below (their top side) and above (their bottom side)
+    const T *pl = strip_block(a.bry, by * a.Mx + lx, 1, H, W), *pr = strip_block(a.bry, by * a.Mx + rx, 0, H, W);
+    const T *pb = strip_block(a.brx, lb * a.Mx + bx, 1, H, W), *pt = strip_block(a.brx, rt * a.Mx + bx, 0, H, W);
     const int64_t base = a.F - H;
     auto inject = [&](int i) {
         const int64_t lev = base + i - 1;
-        const int x0 = cx - i, x1 = cx + i - 1, y0 = cy - i, y1 = cy + i - 1;
-        const int len = 2 * (i - 1);  // the bridges' strips at step i - 1
-        if (len > 0) {
-            for (int t = threadIdx.x; t < 8 * len; t += blockDim.x) {
-                int q, r;
-                div_len(t, len, q, r);
-                const int k = q & 1, which = q >> 1;
-                // 0: y-bridge on the left (its right columns), 1: on the right (its left columns),
-                // 2: x-bridge below (its top rows), 3: above (its bottom rows)
-                if (which < 2) {
-                    const int tb = by * a.Mx + (which == 0 ? lx : rx);
-                    const T v = a.bry[strip_off(tb, which == 0 ? 1 : 0, i - 1, k, H, W) + r];
-                    const int x = which == 0 ? x0 - 1 + k : x1 + k;
-                    f.at(lev, x, cy - i + 1 + r) = v;
-                } else {
-                    const int tb = (which == 2 ? lb : rt) * a.Mx + bx;
-                    const T v = a.brx[strip_off(tb, which == 2 ? 1 : 0, i - 1, k, H, W) + r];
-                    const int y = which == 2 ? y0 - 1 + k : y1 + k;
-                    f.at(lev, cx - i + 1 + r, y) = v;
-                }
-            }
-        }
+        // line q: k = q & 1, which = q >> 1 (0 left, 1 right, 2 below, 3 above), 2(i - 1) entries
+        over_lines<NT, 8>(2 * (i - 1), [&](int q, int r) {
+            const int k = q & 1, which = q >> 1;
+            const T *sb = which == 0 ? pl : which == 1 ? pr : which == 2 ? pb : pt;
+            const T v = sb[strip_at(i - 1, k, W) + r];
+            const int across = (which & 1) ? H + i + k : H - i + k;
+            if (which < 2) f.at(lev, across, H + 2 - i + r) = v;
+            else f.at(lev, H + 2 - i + r, across) = v;
+        });
         // corners: from the x-strips of the four diagonal pyramids of phase p - 1 at step i - 1
+        // (entry = row - the pyramid's first row at that step: H + i above, i - H below)
         if (threadIdx.x < 12) {
             const int c = threadIdx.x / 3, e = threadIdx.x % 3;
             const bool right = c & 1, top = c >> 1;
             const int tp = (top ? rt : lb) * a.Mx + (right ? rx : lx);
-            const int side = right ? 0 : 1;
-            const int ystart = top ? cy + i - 1 : cy - W + i - 1;  // the pyramid's window start
-            const int ycorner = top ? y1 : y0, yout = top ? y1 + 1 : y0 - 1;
-            int x, y, k;
+            int X, Y, k;
             if (e < 2) {  // both new columns at the corner row
                 k = e;
-                x = right ? x1 + k : x0 - 1 + k;
-                y = ycorner;
+                X = right ? H + i + k : H - i + k;
+                Y = top ? H + i : H + 1 - i;
             } else {  // the inner new column, one row further out
                 k = right ? 0 : 1;
-                x = right ? x1 : x0;
-                y = yout;
+                X = right ? H + i : H + 1 - i;
+                Y = top ? H + i + 1 : H - i;
             }
-            f.at(lev, x, y) = a.pin_x[strip_off(tp, side, i - 1, k, H, W) + (y - ystart)];
+            const int entry = top ? Y - (H + i) : Y + H - i;
+            f.at(lev, X, Y) = strip_block(a.pin_x, tp, right ? 0 : 1, H, W)[strip_at(i - 1, k, W) + entry];
         }
     };
     inject(1);
     __syncthreads();
     for (int i = 1; i <= H; ++i) {
-        compute_window(f, base + i, cx - i, cx + i - 1, cy - i, cy + i - 1, a.rx, a.ry);
+        compute_window<NT>(f, base + i, H + 1 - i, H + i, H + 1 - i, H + i, a.rx, a.ry);
         if (i < H) inject(i + 1);
         __syncthreads();
     }
-    if (a.last) {
-        for (int t = threadIdx.x; t < W * W; t += blockDim.x) {
-            const int y = cy - H + t / W, x = cx - H + t % W;
-            a.state[(int64_t)((y + a.ny) % a.ny) * a.nx + (x + a.nx) % a.nx] = f.at(a.F, x, y);
+    if (a.last) {  // the full tile at F, a warp per row
+        const int64_t gx0 = (int64_t)centre2d(a.p, bx, W) - H, gy0 = (int64_t)centre2d(a.p, by, W) - H;
+        for (int Y = 1 + (int)(threadIdx.x >> 5); Y <= W; Y += NT / 32) {
+            T *row = a.state + wrap(gy0 + Y - 1, a.ny) * a.nx;
+            for (int X = 1 + (int)(threadIdx.x & 31); X <= W; X += 32) row[wrap(gx0 + X - 1, a.nx)] = f.at(a.F, X, Y);
         }
         return;
     }
-    pyramid_part(f, a, a.F, blockIdx.x, a.pout_x, a.pout_y);
+    pyramid_part<NT>(f, a, W, H, a.F, blockIdx.x, a.pout_x, a.pout_y);
 }
 
 int cuda_status2d(cudaError_t e) {
@@ -415,6 +459,7 @@ int max_width2d(size_t es) {
 struct sw_handle2d {
     sw_heat2d prob{};
     int W = 0, H = 0, Mx = 0, My = 0;
+    int nt = 0, nt_br = 0;  // threads per swept CTA: Up and octahedra, bridges
     size_t es = 0, smem = 0;
     void *pyrx[2] = {nullptr, nullptr}, *pyry[2] = {nullptr, nullptr};
     void *brx = nullptr, *bry = nullptr;
@@ -465,6 +510,63 @@ void trace2d_end(sw_handle2d *h, int64_t i, cudaStream_t st) {
 unsigned grid2d(int64_t work, int cap) {
     int64_t g = (work + kThreads2D - 1) / kThreads2D;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, cap));
+}
+
+// the swept kernels of one element type, thread count and compiled width: kind 0 Up, 1
+// bridges, 2 octahedra
+template <class T, int NT, int WC> void launch2d_k(int kind, unsigned tiles, size_t smem, cudaStream_t st,
+                                                   const Swept2DArgs<T> &a) {
+    if (kind == 0) k2d_up<T, NT, WC><<<tiles, NT, smem, st>>>(a);
+    else if (kind == 1) k2d_bridges<T, NT, WC><<<dim3(tiles, 2), NT, smem, st>>>(a);
+    else k2d_octa<T, NT, WC><<<tiles, NT, smem, st>>>(a);
+}
+template <class T, int NT> void launch2d_nt(int kind, unsigned tiles, size_t smem, cudaStream_t st,
+                                            const Swept2DArgs<T> &a) {
+    if constexpr (specialised2d<T, NT, 32>()) {
+        if (a.W == 32) return launch2d_k<T, NT, 32>(kind, tiles, smem, st, a);
+    }
+    if constexpr (specialised2d<T, NT, 64>()) {
+        if (a.W == 64) return launch2d_k<T, NT, 64>(kind, tiles, smem, st, a);
+    }
+    if constexpr (specialised2d<T, NT, 128>()) {
+        if (a.W == 128) return launch2d_k<T, NT, 128>(kind, tiles, smem, st, a);
+    }
+    launch2d_k<T, NT, 0>(kind, tiles, smem, st, a);
+}
+template <class T> void launch2d(int kind, int nt, unsigned tiles, size_t smem, cudaStream_t st,
+                                 const Swept2DArgs<T> &a) {
+    if (nt == 128) launch2d_nt<T, 128>(kind, tiles, smem, st, a);
+    else if (nt == kThreads2D) launch2d_nt<T, kThreads2D>(kind, tiles, smem, st, a);
+    else launch2d_nt<T, kThreads2DWide>(kind, tiles, smem, st, a);
+}
+// the dynamic shared-memory limit of the swept kernels of <T, NT, WC>
+template <class T, int NT, int WC> cudaError_t allow_smem2d_k(size_t smem) {
+    const void *fns[3] = {(const void *)k2d_up<T, NT, WC>, (const void *)k2d_bridges<T, NT, WC>,
+                          (const void *)k2d_octa<T, NT, WC>};
+    for (const void *fn : fns) {
+        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+// ... for the kernels a handle of width W may launch at this thread count
+template <class T, int NT> cudaError_t allow_smem2d(int W, size_t smem) {
+    if constexpr (specialised2d<T, NT, 32>()) {
+        if (W == 32) return allow_smem2d_k<T, NT, 32>(smem);
+    }
+    if constexpr (specialised2d<T, NT, 64>()) {
+        if (W == 64) return allow_smem2d_k<T, NT, 64>(smem);
+    }
+    if constexpr (specialised2d<T, NT, 128>()) {
+        if (W == 128) return allow_smem2d_k<T, NT, 128>(smem);
+    }
+    return allow_smem2d_k<T, NT, 0>(smem);
+}
+template <class T> cudaError_t allow_smem2d_all(int W, size_t smem) {
+    cudaError_t e = allow_smem2d<T, 128>(W, smem);
+    if (e == cudaSuccess) e = allow_smem2d<T, kThreads2D>(W, smem);
+    if (e == cudaSuccess) e = allow_smem2d<T, kThreads2DWide>(W, smem);
+    return e;
 }
 
 // `steps` per-step launches, ping-pong between the state and the handle's plane; the
@@ -521,7 +623,7 @@ template <class T> int run2d(sw_handle2d *h, void *state_v, int64_t nsteps, cuda
             a.brx = reinterpret_cast<T *>(h->brx);
             a.bry = reinterpret_cast<T *>(h->bry);
             const unsigned tiles = (unsigned)(h->Mx * h->My);
-            const int nt = swept_threads2d(h->W);
+            const int nt = h->nt;
             for (int64_t p = 0; p <= P; ++p) {
                 a.p = (int)(p & 1) ? 1 : 2;  // only the parity of p matters to the kernels
                 if (p == 0) a.p = 0;
@@ -533,18 +635,15 @@ template <class T> int run2d(sw_handle2d *h, void *state_v, int64_t nsteps, cuda
                 a.pout_y = reinterpret_cast<T *>(h->pyry[p & 1]);
                 if (p == 0) {
                     trace2d_begin(h, launches, 0, st);
-                    if (nt == kThreads2D) k2d_up<T, kThreads2D><<<tiles, nt, h->smem, st>>>(a);
-                    else k2d_up<T, kThreads2DWide><<<tiles, nt, h->smem, st>>>(a);
+                    launch2d<T>(0, nt, tiles, h->smem, st, a);
                     trace2d_end(h, launches++, st);
                     continue;
                 }
                 trace2d_begin(h, launches, 1, st);
-                if (nt == kThreads2D) k2d_bridges<T, kThreads2D><<<dim3(tiles, 2), nt, h->smem, st>>>(a);
-                else k2d_bridges<T, kThreads2DWide><<<dim3(tiles, 2), nt, h->smem, st>>>(a);
+                launch2d<T>(1, h->nt_br, tiles, h->smem, st, a);
                 trace2d_end(h, launches++, st);
                 trace2d_begin(h, launches, p == P ? 4 : 2, st);
-                if (nt == kThreads2D) k2d_octa<T, kThreads2D><<<tiles, nt, h->smem, st>>>(a);
-                else k2d_octa<T, kThreads2DWide><<<tiles, nt, h->smem, st>>>(a);
+                launch2d<T>(2, nt, tiles, h->smem, st, a);
                 trace2d_end(h, launches++, st);
             }
         }
@@ -580,7 +679,7 @@ int sw2d_create(const sw_heat2d *p, sw_handle2d **out) {
     {   // the row-mapping multipliers (the same values on every device; written once per create)
         unsigned magic[kMagicMax + 1];
         magic[0] = 0;
-        magic[1] = 0;  // never used: windows are at least 2 wide
+        magic[1] = 0;  // never used: windows and strips are at least 2 wide, one band needs no division
         for (int w = 2; w <= kMagicMax; ++w) magic[w] = 0xFFFFFFFFu / (unsigned)w + 1u;
         e = cudaMemcpyToSymbol(c_magic, magic, sizeof(magic));
         if (e != cudaSuccess) return fail(cuda_status2d(e));
@@ -592,26 +691,10 @@ int sw2d_create(const sw_heat2d *p, sw_handle2d **out) {
         h->My = (int)(p->ny / h->W);
         if (h->W > max_width2d(h->es)) return fail(SW_ERR_UNSUPPORTED);
         h->smem = smem2d(h->W, h->es);
-        const void *fns[6];
-        if (p->precision == SW_FP64) {
-            fns[0] = (const void *)k2d_up<double, kThreads2D>;
-            fns[1] = (const void *)k2d_bridges<double, kThreads2D>;
-            fns[2] = (const void *)k2d_octa<double, kThreads2D>;
-            fns[3] = (const void *)k2d_up<double, kThreads2DWide>;
-            fns[4] = (const void *)k2d_bridges<double, kThreads2DWide>;
-            fns[5] = (const void *)k2d_octa<double, kThreads2DWide>;
-        } else {
-            fns[0] = (const void *)k2d_up<float, kThreads2D>;
-            fns[1] = (const void *)k2d_bridges<float, kThreads2D>;
-            fns[2] = (const void *)k2d_octa<float, kThreads2D>;
-            fns[3] = (const void *)k2d_up<float, kThreads2DWide>;
-            fns[4] = (const void *)k2d_bridges<float, kThreads2DWide>;
-            fns[5] = (const void *)k2d_octa<float, kThreads2DWide>;
-        }
-        for (const void *fn : fns) {
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
-            if (e != cudaSuccess) return fail(cuda_status2d(e));
-        }
+        h->nt = h->nt_br = swept_threads2d(h->W);
+        e = p->precision == SW_FP64 ? allow_smem2d_all<double>(h->W, h->smem)
+                                    : allow_smem2d_all<float>(h->W, h->smem);
+        if (e != cudaSuccess) return fail(cuda_status2d(e));
         // per buffer: tiles x 2 sides x H steps x 2 x W values
         const size_t bytes = size_t(h->Mx) * h->My * 2 * h->H * 2 * h->W * h->es;
         void **bufs[6] = {&h->pyrx[0], &h->pyrx[1], &h->pyry[0], &h->pyry[1], &h->brx, &h->bry};
@@ -650,6 +733,19 @@ int sw2d_run(sw_handle2d *h, void *state, int64_t nsteps, void *stream) {
 int64_t sw2d_last_launch_count(const sw_handle2d *h) { return h ? h->last_launches : 0; }
 
 int32_t sw2d_tile_width(const sw_handle2d *h) { return h ? h->W : 0; }
+
+int sw2d_set_threads(sw_handle2d *h, int32_t threads, int32_t bridge_threads) {
+    if (!h || h->prob.method != SW_SWEPT) return SW_ERR_BAD_ARG;
+    if (threads == 0) threads = swept_threads2d(h->W);
+    if (bridge_threads == 0) bridge_threads = swept_threads2d(h->W);
+    auto ok = [](int32_t t) { return t == 128 || t == kThreads2D || t == kThreads2DWide; };
+    if (!ok(threads) || !ok(bridge_threads)) return SW_ERR_BAD_ARG;
+    h->nt = threads;
+    h->nt_br = bridge_threads;
+    return SW_OK;
+}
+
+int32_t sw2d_threads(const sw_handle2d *h, int32_t bridges) { return h ? (bridges ? h->nt_br : h->nt) : 0; }
 
 int sw2d_set_timing(sw_handle2d *h, int64_t capacity) {
     if (!h || capacity < 0 || capacity > (int64_t(1) << 24)) return SW_ERR_BAD_ARG;

@@ -36,6 +36,8 @@ def main(argv=None):
     ap.add_argument("--width", type=int, default=1024)
     ap.add_argument("--r", type=float, default=0.3)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--threads", type=int, default=0, help="heat2d swept: threads per CTA (0: the default)")
+    ap.add_argument("--bridge-threads", type=int, default=0, help="heat2d swept: threads per bridges CTA")
     ap.add_argument("--generic", action="store_true", help="force the generic phase kernel (SW_FLAG_GENERIC)")
     ap.add_argument("--flags", type=int, default=0, help="further SW_FLAG_* bits (e.g. 8: flattened Euler)")
     a = ap.parse_args(argv)
@@ -120,6 +122,8 @@ def run2d(a) -> int:
     st = fresh.clone()
     t = None
     with S.Handle2D(p) as h:
+        if a.method == "swept":
+            h.sw2d_set_threads(a.threads, a.bridge_threads)
         for _ in range(a.repeat):
             st.copy_(fresh)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -131,7 +135,8 @@ def run2d(a) -> int:
             t = e0.elapsed_time(e1) / 1e3
         launches = h.sw2d_last_launch_count()
     print(json.dumps({"scheme": "heat2d", "precision": a.precision, "method": a.method, "nx": a.nx, "ny": a.ny,
-                      "steps": a.steps, "width": a.width, "launches": launches, "seconds": t,
+                      "steps": a.steps, "width": a.width, "threads": a.threads,
+                      "bridge_threads": a.bridge_threads, "launches": launches, "seconds": t,
                       "gcell_updates_per_s": a.nx * a.ny * a.steps / t / 1e9}))
     return 0
 

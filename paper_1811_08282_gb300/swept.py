@@ -15,7 +15,7 @@ from dataclasses import dataclass
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libswept.so")
 
-ABI_VERSION = 4  # SW_ABI_VERSION of include/swept.h
+ABI_VERSION = 5  # SW_ABI_VERSION of include/swept.h
 SW_HEAT, SW_EULER = 0, 1
 SW_FP64, SW_FP32, SW_FP32_COMP = 0, 1, 2
 SW_PERIODIC, SW_TRANSMISSIVE = 0, 1
@@ -42,7 +42,7 @@ EXPORTS = (
     "sw_batch_create", "sw_batch_run", "sw_batch_status", "sw_batch_items", "sw_batch_debug",
     "sw_batch_destroy", "sw_batch_set_threads", "sw_autotune", "sw_hybrid_split", "sw_run_hybrid", "sw_debug_corrupt_guard",
     "sw2d_create", "sw2d_destroy", "sw2d_run", "sw2d_last_launch_count", "sw2d_tile_width", "sw2d_set_timing",
-    "sw2d_launch_times",
+    "sw2d_launch_times", "sw2d_set_threads", "sw2d_threads",
 )
 
 
@@ -129,6 +129,8 @@ def load(path: str = LIB_PATH):
         "sw2d_run": ([vp, vp, i64, vp], ctypes.c_int),
         "sw2d_last_launch_count": ([vp], i64),
         "sw2d_tile_width": ([vp], i32),
+        "sw2d_set_threads": ([vp, i32, i32], ctypes.c_int),
+        "sw2d_threads": ([vp, i32], i32),
         "sw2d_set_timing": ([vp, i64], ctypes.c_int),
         "sw2d_launch_times": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32), i64], i64),
     }
@@ -438,6 +440,12 @@ class Handle2D:
 
     def sw2d_tile_width(self) -> int:
         return int(load().sw2d_tile_width(self._h))
+
+    def sw2d_set_threads(self, threads: int, bridge_threads: int = 0) -> None:
+        _check(load().sw2d_set_threads(self._h, int(threads), int(bridge_threads)), "sw2d_set_threads")
+
+    def sw2d_threads(self, bridges: bool = False) -> int:
+        return int(load().sw2d_threads(self._h, int(bool(bridges))))
 
     def sw2d_set_timing(self, capacity: int) -> None:
         _check(load().sw2d_set_timing(self._h, int(capacity)), "sw2d_set_timing")

@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert S.sw_abi_version() == S.ABI_VERSION == 4
+    assert S.sw_abi_version() == S.ABI_VERSION == 5
     for code in (0, 1, -1, -2, -3, -4, -5, -6):
         assert S.status_string(code) and S.status_string(code) != "unknown status"
     assert S.status_string(12345) == "unknown status"

@@ -77,6 +77,47 @@ def test_constant_along_y_equals_the_1d_run(prec):
         assert np.array_equal(got[j], one)
 
 
+@pytest.mark.parametrize("prec", [S.SW_FP64, S.SW_FP32])
+@pytest.mark.parametrize("W", [16, 32, 64, 128])
+def test_threads_per_cta_give_the_same_bits(prec, W):
+    # every thread count computes the same cells with the same arithmetic (the FP32 walker's
+    # bands and the strip lines change with it; with 128 threads a warp takes several lines)
+    if prec == S.SW_FP64 and W > 118:
+        pytest.skip("an FP64 frame of W = 128 exceeds the shared memory (FP64 holds W <= 118)")
+    nx, ny, steps = 4 * W, 3 * W, 3 * (W // 2) + 5
+    u0 = I.heat2d_initial(I.heat2d_modes(nx, ny, 6, seed=W, kmax=8))
+    p = S.Heat2D(precision=prec, method=S.SW_SWEPT, tile_width=W, nx=nx, ny=ny, rx=0.19, ry=0.23)
+    ref, _ = run2d(S.Heat2D(precision=prec, method=S.SW_PERSTEP, nx=nx, ny=ny, rx=0.19, ry=0.23), u0, steps)
+    import torch
+    dt = torch.float64 if prec == S.SW_FP64 else torch.float32
+    for nt, nb in ((128, 128), (256, 128), (128, 256), (256, 256), (1024, 256), (256, 1024)):
+        st = torch.as_tensor(u0.reshape(-1), device="cuda").to(dt).clone()
+        with S.Handle2D(p) as h:
+            h.sw2d_set_threads(nt, nb)
+            assert h.sw2d_threads() == nt and h.sw2d_threads(bridges=True) == nb
+            h.sw2d_run(st, steps)
+        torch.cuda.synchronize()
+        assert np.array_equal(st.double().cpu().numpy().reshape(ny, nx), ref), (nt, nb)
+
+
+def test_set_threads_refuses_other_counts():
+    p = S.Heat2D(precision=S.SW_FP32, method=S.SW_SWEPT, tile_width=32, nx=128, ny=128, rx=0.2, ry=0.2)
+    with S.Handle2D(p) as h:
+        assert h.sw2d_threads() == 256 and h.sw2d_threads(bridges=True) == 256
+        for bad in (64, 512, 100, -1):
+            for args in ((bad, 0), (0, bad)):
+                with pytest.raises(S.SweptError) as ei:
+                    h.sw2d_set_threads(*args)
+                assert ei.value.code == S.SW_ERR_BAD_ARG
+        h.sw2d_set_threads(128, 1024)
+        h.sw2d_set_threads(0, 0)
+        assert h.sw2d_threads() == 256 and h.sw2d_threads(bridges=True) == 256
+    with S.Handle2D(S.Heat2D(precision=S.SW_FP32, method=S.SW_PERSTEP, nx=128, ny=128, rx=0.2, ry=0.2)) as h:
+        with pytest.raises(S.SweptError):
+            h.sw2d_set_threads(256)
+        assert h.sw2d_threads() == 0
+
+
 def test_transmissive_perstep_matches_oracle():
     nx, ny, steps = 96, 80, 60
     rng = np.random.default_rng(5)
