@@ -58,14 +58,20 @@ template <class T> struct Ops2D;
 template <> struct Ops2D<double> { using O = OpsD; };
 template <> struct Ops2D<float> { using O = OpsF; };
 
-constexpr int kThreads2D = 256;       // per-step kernel; swept kernels at W < 128
-constexpr int kThreads2DWide = 1024;  // swept kernels at W >= 128: one CTA per SM fits the frame
+constexpr int kThreads2D = 256;       // per-step kernel; FP64 swept kernels; FP32 bridges at W >= 128
+constexpr int kThreads2DWide = 1024;  // FP32 Up / octahedra at W >= 128: one CTA per SM fits the frame
 
-// Threads of a swept CTA by default: the frame of W >= 128 leaves room for one CTA per SM,
-// which then takes all the warps it can. The swept kernels are instantiated for 128, 256
-// and 1024 threads (sw2d_set_threads), each with a launch bound that keeps the resident-CTA
-// count the frame's shared memory allows at W = 64 (FP32: 6 per SM, FP64: 3; one at 1024).
-__host__ __device__ constexpr int swept_threads2d(int W) { return W >= 128 ? kThreads2DWide : kThreads2D; }
+// Threads of a swept CTA. The kernels are instantiated for 128, 256 and 1024 threads
+// (sw2d_set_threads), each with a launch bound that keeps the resident-CTA count the frame's
+// shared memory allows at W = 64 (FP32: 6 per SM, FP64: 3; one at 1024). Defaults, measured
+// on 8192^2 x 2048 steps: FP32 below W = 128, 128 threads (six CTAs per SM at W = 64: fewer
+// threads give each more cells per level against the per-level costs; 843 against 730
+// Gcell-updates/s with 256); FP32 from W = 128 (one CTA per SM), 1024 for the Up and
+// octahedra launches and 256 for the bridges; FP64, 256 (bound by its pipe; 90.4 against
+// 89.4 with 128).
+__host__ __device__ constexpr int swept_threads2d(size_t es, int W, bool bridges) {
+    return es == 8 ? kThreads2D : (W < 128 ? 128 : (bridges ? kThreads2D : kThreads2DWide));
+}
 template <class T, int NT> constexpr int min_ctas2d() { return NT >= kThreads2DWide ? 1 : (sizeof(T) == 4 ? 6 : 3); }
 
 // Swept kernels compiled for one tile width WC (0: W read from the arguments). With W a
@@ -193,7 +199,8 @@ __device__ __forceinline__ int strip_at(int i, int k, int W) { return (i * 2 + k
 template <class T> struct Frame {
     T *s;
     int RS, slot;
-    __device__ __forceinline__ T &at(int64_t lev, int X, int Y) const { return s[((int)lev & 1) * slot + Y * RS + X]; }
+    __device__ __forceinline__ int idx(int64_t lev, int X, int Y) const { return ((int)lev & 1) * slot + Y * RS + X; }
+    __device__ __forceinline__ T &at(int64_t lev, int X, int Y) const { return s[idx(lev, X, Y)]; }
 };
 
 // `LINES` strip lines of `len` elements each over a block of NT threads, packed: element t
@@ -207,6 +214,43 @@ template <int NT, int LINES, class Fn> __device__ __forceinline__ void over_line
         fn(q, r);
     }
 }
+
+// A strip injection in two halves, so that the loads of a level's inputs overlap the compute
+// of the level before: fetch() reads this thread's first E entries of the LINES x len strip
+// entries (packed as in over_lines) into registers together with their frame indices, put()
+// writes them into the frame after the compute and takes any entries beyond E x NT directly.
+// get(q, r): the entry's value; where(q, r): its index in the frame's storage.
+template <class T, int NT, int LINES, int E> struct Staged {
+    T v[E];
+    int pos[E];
+    template <class Get, class Where> __device__ __forceinline__ void fetch(int len, Get &&get, Where &&where) {
+        const unsigned m = c_magic[len];
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const int t = (int)threadIdx.x + j * NT;
+            v[j] = T(0);
+            pos[j] = -1;
+            if (t < LINES * len) {
+                const int q = (int)__umulhi((unsigned)t, m), r = t - q * len;
+                v[j] = get(q, r);
+                pos[j] = where(q, r);
+            }
+        }
+    }
+    template <class Get, class Where>
+    __device__ __forceinline__ void put(T *s, int len, Get &&get, Where &&where) const {
+#pragma unroll
+        for (int j = 0; j < E; ++j)
+            if (pos[j] >= 0) s[pos[j]] = v[j];
+        if (LINES * len > E * NT) {
+            const unsigned m = c_magic[len];
+            for (int t = (int)threadIdx.x + E * NT; t < LINES * len; t += NT) {
+                const int q = (int)__umulhi((unsigned)t, m), r = t - q * len;
+                s[where(q, r)] = get(q, r);
+            }
+        }
+    }
+};
 
 __device__ __forceinline__ int64_t wrap(int64_t x, int64_t n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
@@ -345,22 +389,25 @@ __global__ void __launch_bounds__(NT, (min_ctas2d<T, NT>())) k2d_bridges(Swept2D
     // step i's inputs at level base + i - 1: the pyramids' strips at step i - 1, all of
     // their W - 2(i-1) entries (rows i + r for an x-bridge, columns for a y-bridge); line q:
     // k = q & 1, high-side neighbour q >> 1
-    auto inject = [&](int i) {
-        over_lines<NT, 4>(W - 2 * (i - 1), [&](int q, int r) {
-            const int k = q & 1, hiside = q >> 1;
-            const T v = (hiside ? phi : plo)[strip_at(i - 1, k, W) + r];
-            const int across = hiside ? H + i + k : H - i + k;
-            if (xb) f.at(base + i - 1, across, i + r) = v;
-            else f.at(base + i - 1, i + r, across) = v;
-        });
+    // (staged: step i + 1's strip loads are issued before step i's compute and written after it,
+    // to positions of the slot being written that lie outside step i's window)
+    int si = 1;  // the step whose inputs get() / where() address
+    auto get = [&](int q, int r) { return ((q >> 1) ? phi : plo)[strip_at(si - 1, q & 1, W) + r]; };
+    auto where = [&](int q, int r) {
+        const int across = (q >> 1) ? H + si + (q & 1) : H - si + (q & 1);
+        return xb ? f.idx(base + si - 1, across, si + r) : f.idx(base + si - 1, si + r, across);
     };
-    inject(1);
+    Staged<T, NT, 4, 2> stage;
+    stage.fetch(W, get, where);
+    stage.put(f.s, W, get, where);
     __syncthreads();
     for (int i = 1; i < H; ++i) {
+        si = i + 1;
+        if (si < H) stage.fetch(W - 2 * i, get, where);
         // the widening direction's window [H + 1 - i, H + i], the narrowing one's [i + 1, W - i]
         if (xb) compute_window<NT>(f, base + i, H + 1 - i, H + i, i + 1, W - i, a.rx, a.ry);
         else compute_window<NT>(f, base + i, i + 1, W - i, H + 1 - i, H + i, a.rx, a.ry);
-        if (i + 1 < H) inject(i + 1);  // other positions of the slot being written
+        if (si < H) stage.put(f.s, W - 2 * i, get, where);
         __syncthreads();
         // export the edges along the widening direction's normal: an x-bridge its bottom and
         // top two rows (2i columns), a y-bridge its left and right two columns (2i rows);
@@ -390,19 +437,24 @@ __global__ void __launch_bounds__(NT, (min_ctas2d<T, NT>())) k2d_octa(Swept2DArg
     const T *pl = strip_block(a.bry, by * a.Mx + lx, 1, H, W), *pr = strip_block(a.bry, by * a.Mx + rx, 0, H, W);
     const T *pb = strip_block(a.brx, lb * a.Mx + bx, 1, H, W), *pt = strip_block(a.brx, rt * a.Mx + bx, 0, H, W);
     const int64_t base = a.F - H;
-    auto inject = [&](int i) {
-        const int64_t lev = base + i - 1;
-        // line q: k = q & 1, which = q >> 1 (0 left, 1 right, 2 below, 3 above), 2(i - 1) entries
-        over_lines<NT, 8>(2 * (i - 1), [&](int q, int r) {
-            const int k = q & 1, which = q >> 1;
-            const T *sb = which == 0 ? pl : which == 1 ? pr : which == 2 ? pb : pt;
-            const T v = sb[strip_at(i - 1, k, W) + r];
-            const int across = (which & 1) ? H + i + k : H - i + k;
-            if (which < 2) f.at(lev, across, H + 2 - i + r) = v;
-            else f.at(lev, H + 2 - i + r, across) = v;
-        });
-        // corners: from the x-strips of the four diagonal pyramids of phase p - 1 at step i - 1
-        // (entry = row - the pyramid's first row at that step: H + i above, i - H below)
+    // step i's inputs at level base + i - 1, staged as in the bridges: line q of 2(i - 1)
+    // entries, k = q & 1, which = q >> 1 (0 left, 1 right, 2 below, 3 above)
+    int si = 1;
+    auto get = [&](int q, int r) {
+        const int which = q >> 1;
+        const T *sb = which == 0 ? pl : which == 1 ? pr : which == 2 ? pb : pt;
+        return sb[strip_at(si - 1, q & 1, W) + r];
+    };
+    auto where = [&](int q, int r) {
+        const int across = (q & 2) ? H + si + (q & 1) : H - si + (q & 1);
+        return (q >> 1) < 2 ? f.idx(base + si - 1, across, H + 2 - si + r) : f.idx(base + si - 1, H + 2 - si + r, across);
+    };
+    // corners: from the x-strips of the four diagonal pyramids of phase p - 1 at step i - 1
+    // (entry = row - the pyramid's first row at that step: H + i above, i - H below); threads
+    // 0..11, three cells per corner
+    T cv = T(0);
+    int cpos = -1;
+    auto corner = [&](int i) {
         if (threadIdx.x < 12) {
             const int c = threadIdx.x / 3, e = threadIdx.x % 3;
             const bool right = c & 1, top = c >> 1;
@@ -418,14 +470,25 @@ __global__ void __launch_bounds__(NT, (min_ctas2d<T, NT>())) k2d_octa(Swept2DArg
                 Y = top ? H + i + 1 : H - i;
             }
             const int entry = top ? Y - (H + i) : Y + H - i;
-            f.at(lev, X, Y) = strip_block(a.pin_x, tp, right ? 0 : 1, H, W)[strip_at(i - 1, k, W) + entry];
+            cv = strip_block(a.pin_x, tp, right ? 0 : 1, H, W)[strip_at(i - 1, k, W) + entry];
+            cpos = f.idx(base + i - 1, X, Y);
         }
     };
-    inject(1);
+    Staged<T, NT, 8, 2> stage;
+    corner(1);  // step 1: no bridge entries yet (length 0)
+    if (cpos >= 0) f.s[cpos] = cv;
     __syncthreads();
     for (int i = 1; i <= H; ++i) {
+        si = i + 1;
+        if (si <= H) {
+            stage.fetch(2 * i, get, where);
+            corner(si);
+        }
         compute_window<NT>(f, base + i, H + 1 - i, H + i, H + 1 - i, H + i, a.rx, a.ry);
-        if (i < H) inject(i + 1);
+        if (si <= H) {
+            stage.put(f.s, 2 * i, get, where);
+            if (cpos >= 0) f.s[cpos] = cv;
+        }
         __syncthreads();
     }
     if (a.last) {  // the full tile at F, a warp per row
@@ -691,7 +754,8 @@ int sw2d_create(const sw_heat2d *p, sw_handle2d **out) {
         h->My = (int)(p->ny / h->W);
         if (h->W > max_width2d(h->es)) return fail(SW_ERR_UNSUPPORTED);
         h->smem = smem2d(h->W, h->es);
-        h->nt = h->nt_br = swept_threads2d(h->W);
+        h->nt = swept_threads2d(h->es, h->W, false);
+        h->nt_br = swept_threads2d(h->es, h->W, true);
         e = p->precision == SW_FP64 ? allow_smem2d_all<double>(h->W, h->smem)
                                     : allow_smem2d_all<float>(h->W, h->smem);
         if (e != cudaSuccess) return fail(cuda_status2d(e));
@@ -736,8 +800,8 @@ int32_t sw2d_tile_width(const sw_handle2d *h) { return h ? h->W : 0; }
 
 int sw2d_set_threads(sw_handle2d *h, int32_t threads, int32_t bridge_threads) {
     if (!h || h->prob.method != SW_SWEPT) return SW_ERR_BAD_ARG;
-    if (threads == 0) threads = swept_threads2d(h->W);
-    if (bridge_threads == 0) bridge_threads = swept_threads2d(h->W);
+    if (threads == 0) threads = swept_threads2d(h->es, h->W, false);
+    if (bridge_threads == 0) bridge_threads = swept_threads2d(h->es, h->W, true);
     auto ok = [](int32_t t) { return t == 128 || t == kThreads2D || t == kThreads2DWide; };
     if (!ok(threads) || !ok(bridge_threads)) return SW_ERR_BAD_ARG;
     h->nt = threads;

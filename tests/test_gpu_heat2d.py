@@ -103,7 +103,7 @@ def test_threads_per_cta_give_the_same_bits(prec, W):
 def test_set_threads_refuses_other_counts():
     p = S.Heat2D(precision=S.SW_FP32, method=S.SW_SWEPT, tile_width=32, nx=128, ny=128, rx=0.2, ry=0.2)
     with S.Handle2D(p) as h:
-        assert h.sw2d_threads() == 256 and h.sw2d_threads(bridges=True) == 256
+        assert h.sw2d_threads() == 128 and h.sw2d_threads(bridges=True) == 128
         for bad in (64, 512, 100, -1):
             for args in ((bad, 0), (0, bad)):
                 with pytest.raises(S.SweptError) as ei:
@@ -111,7 +111,13 @@ def test_set_threads_refuses_other_counts():
                 assert ei.value.code == S.SW_ERR_BAD_ARG
         h.sw2d_set_threads(128, 1024)
         h.sw2d_set_threads(0, 0)
+        assert h.sw2d_threads() == 128 and h.sw2d_threads(bridges=True) == 128
+    p64 = S.Heat2D(precision=S.SW_FP64, method=S.SW_SWEPT, tile_width=32, nx=128, ny=128, rx=0.2, ry=0.2)
+    with S.Handle2D(p64) as h:
         assert h.sw2d_threads() == 256 and h.sw2d_threads(bridges=True) == 256
+    p128 = S.Heat2D(precision=S.SW_FP32, method=S.SW_SWEPT, tile_width=128, nx=256, ny=256, rx=0.2, ry=0.2)
+    with S.Handle2D(p128) as h:
+        assert h.sw2d_threads() == 1024 and h.sw2d_threads(bridges=True) == 256
     with S.Handle2D(S.Heat2D(precision=S.SW_FP32, method=S.SW_PERSTEP, nx=128, ny=128, rx=0.2, ry=0.2)) as h:
         with pytest.raises(S.SweptError):
             h.sw2d_set_threads(256)
