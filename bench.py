@@ -85,6 +85,7 @@ def initial_state():
 KERNEL_SOURCES = {
     "k_heat_fold": ("common.cuh", "heat.cuh", "flanks.cuh", "fp64_soft.cuh", "fold_heat.cuh"),
     "k_swept_phase": ("common.cuh", "heat.cuh", "heat_policy.cuh", "flanks.cuh", "swept_phase.cuh"),
+    "k2d": ("common.cuh", "heat.cuh", "fp64_soft.cuh", "fp64_soft2d.cuh", "heat2d.cu"),
 }
 
 
@@ -299,6 +300,7 @@ def run_ours(args):
     except Exception:
         pipes = None
     fp64_rate = pipes["fp64_fma"] if pipes else FP64_INST_PER_S
+    alu_rate = pipes["int_alu"] if pipes else ALU_LANE_INST_PER_S
     peak, peak_source = FP64_PEAK_TFLOPS, \
         "FP64 1.25 TFLOP/s class: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz (nominal, recipe)"
     fp64_ipu = recorded(kname, f"{kname}.heat_fp64.w{best_w}", "fp64_inst_per_update") if fold else None
@@ -359,7 +361,7 @@ def run_ours(args):
     compare = {}
     if world == 1:
         compare_legs(args, S, problem, timed_run, u0_dev, best_w, value, final, flush, stream, dev, compare,
-                     modes, r, u0, fp64_rate)
+                     modes, r, u0, fp64_rate, alu_rate)
     cpu = compare.pop("_cpu_baseline", None)
 
     line = {
@@ -379,7 +381,7 @@ def run_ours(args):
 
 
 def compare_legs(args, S, problem, timed_run, u0_dev, best_w, value, final, flush, stream, dev, compare,
-                 modes, r, u0, fp64_rate):
+                 modes, r, u0, fp64_rate, alu_rate):
     """Every comparison of the JSON line besides the headline (single-GPU runs)."""
     import torch
     world = 1
@@ -415,7 +417,7 @@ def compare_legs(args, S, problem, timed_run, u0_dev, best_w, value, final, flus
     sod_out = euler_leg(S, timed_run, "sod")
     rie_out = euler_leg(S, timed_run, "riemann")
     # the swept rule in two dimensions (heat, 8192 x 8192)
-    compare["heat2d_8192^2"] = heat2d_leg(S, flush, stream, fp64_rate)
+    compare["heat2d_8192^2"] = heat2d_leg(S, flush, stream, fp64_rate, alu_rate)
     # batched: 4096 problems at the configured 10,000 steps
     batch_leg, batch_out = batched_leg(S, stream)
     compare["batched_4096"] = batch_leg
@@ -612,10 +614,21 @@ def heat_precision_leg(S, timed_run):
 
 H2D_N, H2D_STEPS, H2D_R, H2D_SEED = 8192, 2048, 0.2, 6
 H2D_FLOPS_PER_UPDATE = 10  # a + b, d + e, fma(-2, u, .) x 2, fma(ry, ., u), fma(rx, ., .)
-H2D_FP64_INST_PER_UPDATE = 6
 
 
-def heat2d_leg(S, flush, stream, fp64_rate):
+def pipe_ceiling2d(key, fp64_rate, alu_rate):
+    """Updates/s ceiling of an FP64 2D kernel that runs part of its cells on the integer
+    pipes: the busier of the FP64 and ALU pipes at their measured rates for the kernel's
+    instruction mix (ncu counts in profiles/traffic.txt), with the counts used; None when
+    the kernel changed since they were taken."""
+    f = recorded("k2d", key, "fp64_inst_per_update")
+    a = recorded("k2d", key, "alu_inst_per_update")
+    if not (f and a):
+        return None, None, None
+    return min(fp64_rate / f, alu_rate / a), f, a
+
+
+def heat2d_leg(S, flush, stream, fp64_rate, alu_rate):
     """Heat in two dimensions (the 5-point extension of Section 6's future work): periodic
     8192 x 8192, rx = ry = 0.2, 16 separable modes, 2048 steps; per precision the swept run
     (W tuned on short runs) against the per-step kernel, the error against the oracle's
@@ -678,17 +691,26 @@ def heat2d_leg(S, flush, stream, fp64_rate):
             form["octahedra_share_of_phase"] = statistics.mean(oc) / (statistics.mean(br) + statistics.mean(oc))
             if prec == S.SW_FP64:
                 achieved = updates * H2D_FLOPS_PER_UPDATE / phase_s / 1e12
-                # the kernel's ceiling: the FP64 pipe at its measured rate, 6 FP64 instructions per update
-                ceiling = fp64_rate / H2D_FP64_INST_PER_UPDATE * H2D_FLOPS_PER_UPDATE / 1e12
-                res["roofline"] = {"bound": "fp64", "achieved": achieved, "peak": ceiling, "unit": "TFLOP/s",
-                                   "frac": achieved / ceiling, "traffic": None,
-                                   "kernel": f"k2d_bridges<double> + k2d_octa<double> (one swept phase, W = {W})",
-                                   "flops_per_update": H2D_FLOPS_PER_UPDATE,
-                                   "fp64_pipe_nominal": FP64_PEAK_TFLOPS,
-                                   "frac_of_fp64_pipe_nominal": achieved / FP64_PEAK_TFLOPS,
-                                   "peak_source": f"FP64 pipe at its measured rate ({fp64_rate / 1e9:.0f} G DFMA/s, chain "
-                                                  "probe) / 6 FP64 instructions per update (2 add, 4 FMA), in "
-                                                  "flops at 10 per update"}
+                ceil, fi, ai = pipe_ceiling2d(f"k2d.phase_fp64.w{W}", fp64_rate, alu_rate)
+                bpu = recorded("k2d", f"k2d.phase_fp64.w{W}", "bytes_per_update")
+                peak = ceil * H2D_FLOPS_PER_UPDATE / 1e12 if ceil else None
+                res["roofline"] = {
+                    "bound": "fp64+alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": (achieved / peak) if peak else None,
+                    "traffic": bpu * updates if bpu else None,
+                    "kernel": f"k2d_bridges<double> + k2d_octa<double> (one swept phase, W = {W})",
+                    "flops_per_update": H2D_FLOPS_PER_UPDATE,
+                    "fp64_pipe_nominal": FP64_PEAK_TFLOPS,
+                    "peak_source": (f"half the cells on the integer pipes: min(FP64 pipe {fp64_rate / 1e9:.0f} G/s / "
+                                    f"{fi} FP64 instr per update, ALU pipe {alu_rate / 1e12:.1f} T/s / {ai} ALU instr "
+                                    f"per update), measured rates (chain probes), ncu counts of the phase "
+                                    f"(profiles/traffic.txt), in flops at 10 per update") if peak else
+                                   "instruction counts not current for this kernel"}
+        if prec == S.SW_FP64:
+            ceil, fi, ai = pipe_ceiling2d("k2d.step_fp64", fp64_rate, alu_rate)
+            if ceil:
+                form["perstep_ceiling_gups"] = ceil / 1e9
+                form["perstep_frac_of_ceiling"] = form["perstep"] / (ceil / 1e9)
         res[pn] = form
     return res
 

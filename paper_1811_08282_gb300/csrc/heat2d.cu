@@ -37,6 +37,7 @@
 
 #include "../../include/swept.h"
 #include "common.cuh"
+#include "fp64_soft2d.cuh"
 
 using namespace sw;
 
@@ -57,6 +58,24 @@ __device__ __forceinline__ typename O::T heat2d_update(typename O::T rx, typenam
 template <class T> struct Ops2D;
 template <> struct Ops2D<double> { using O = OpsD; };
 template <> struct Ops2D<float> { using O = OpsF; };
+
+// FP64: half the cells go through the integer pipes (soft64::heat2d_update, the same bits as
+// the FP64 instructions give; FP64 issues at 1/32 of the integer rate on GB300, so a 2D update
+// of 6 FP64 instructions leaves the integer pipes idle). A cell outside the integer path's
+// range (mixed signs, a neighbour far from u in magnitude, a result leaving u's binade) is
+// evaluated here instead, out of line, so that its FP64 instructions issue only when a lane
+// of the warp needs them.
+__device__ __noinline__ double heat2d_update_fp64(double rx, double ry, double a, double b, double u, double d,
+                                                 double e) {
+    return heat2d_update<OpsD>(rx, ry, a, b, u, d, e);
+}
+__device__ __forceinline__ double heat2d_update_int(const soft64::HeatR &hx, const soft64::HeatR &hy, double rx,
+                                                    double ry, double a, double b, double u, double d, double e) {
+    bool ok;
+    const uint64_t v = soft64::heat2d_update(hx, hy, soft64::bits(a), soft64::bits(b), soft64::bits(u),
+                                             soft64::bits(d), soft64::bits(e), ok);
+    return ok ? soft64::value(v) : heat2d_update_fp64(rx, ry, a, b, u, d, e);
+}
 
 constexpr int kThreads2D = 256;       // per-step kernel; FP64 swept kernels; FP32 bridges at W >= 128
 constexpr int kThreads2DWide = 1024;  // FP32 Up / octahedra at W >= 128: one CTA per SM fits the frame
@@ -126,10 +145,12 @@ template <> struct RowIO<double, 4, true> {
 // One step over the whole grid: each thread takes V consecutive cells of a row (item
 // = row * (nx / V) + chunk, grid-stride); x-neighbours at the chunk's ends and the
 // rows above and below come through the caches. VEC: the row pieces move as 16-byte
-// vectors (the launcher checks the alignment of the state and of nx).
+// vectors (the launcher checks the alignment of the state and of nx). FP64 with V = 4:
+// cells 1 and 3 of every thread on the integer pipes, 0 and 2 on the FP64 pipe.
 template <class T, int V, bool VEC>
 __global__ void __launch_bounds__(kThreads2D) k2d_step(const T *__restrict__ in, T *__restrict__ out, int64_t nx,
-                                                       int64_t ny, T rx, T ry, int periodic) {
+                                                       int64_t ny, T rx, T ry, int periodic, soft64::HeatR hx,
+                                                       soft64::HeatR hy) {
     using O = typename Ops2D<T>::O;
     using IO = RowIO<T, V, VEC>;
     const int64_t chunks = nx / V, items = chunks * ny;
@@ -150,6 +171,12 @@ __global__ void __launch_bounds__(kThreads2D) k2d_step(const T *__restrict__ in,
         for (int k = 0; k < V; ++k) {
             const T a = k > 0 ? c[k - 1] : left;
             const T b = k < V - 1 ? c[k + 1] : right;
+            if constexpr (sizeof(T) == 8 && V == 4) {
+                if (k & 1) {
+                    o[k] = heat2d_update_int(hx, hy, rx, ry, a, b, c[k], d[k], e[k]);
+                    continue;
+                }
+            }
             o[k] = heat2d_update<O>(rx, ry, a, b, c[k], d[k], e[k]);
         }
         IO::store(out + j * nx + i0, o);
@@ -168,6 +195,7 @@ template <class T> struct Swept2DArgs {
     T *pout_x, *pout_y;      // pyramid strips of phase p
     T *brx, *bry;            // bridge strips of phase p
     T rx, ry;
+    soft64::HeatR hrx, hry;  // rx, ry unpacked for the integer path (FP64)
 };
 
 __device__ __forceinline__ int centre2d(int p, int b, int W) { return b * W + ((p & 1) ? 0 : W / 2); }
@@ -269,7 +297,7 @@ __device__ __forceinline__ int64_t wrap(int64_t x, int64_t n) { return x < 0 ? x
 //    any of them is stored.
 template <int NT, class T>
 __device__ __forceinline__ void compute_window(const Frame<T> &f, int64_t lev, int X0, int X1, int Y0, int Y1, T rx,
-                                               T ry) {
+                                               T ry, const soft64::HeatR &hx, const soft64::HeatR &hy) {
     using O = typename Ops2D<T>::O;
     const int RS = f.RS;
     const T *src = f.s + (((int)lev - 1) & 1) * f.slot;
@@ -278,13 +306,25 @@ __device__ __forceinline__ void compute_window(const Frame<T> &f, int64_t lev, i
     if constexpr (sizeof(T) == 8) {
         const unsigned cnt = w * h, m = c_magic[w];
         const int org = Y0 * RS + X0;
-#pragma unroll 4
-        // the stride is read from blockDim, not the compile-time NT: with a constant stride
-        // the unrolled loop ran 7 % slower (FP64, W = 64, 8192^2), the same cells in the same order
-        for (unsigned t = threadIdx.x; t < cnt; t += blockDim.x) {
-            const unsigned yy = __umulhi(t, m), xx = t - yy * w;
-            const int q = org + (int)yy * RS + (int)xx;
-            dst[q] = heat2d_update<O>(rx, ry, src[q - 1], src[q + 1], src[q], src[q - RS], src[q + RS]);
+        // Cells in pairs t, t + nt: the first on the integer pipes, the second on the FP64 pipe
+        // (uniform over the warp; a window smaller than two rounds of the block thus leans to the
+        // integer pipes, which the FP64-bound kernel has to spare). The stride is read from
+        // blockDim, not the compile-time NT: with a constant stride the unrolled loop ran 7 %
+        // slower (FP64 pipe only, W = 64, 8192^2).
+        const unsigned nt = blockDim.x;
+#pragma unroll 2
+        for (unsigned t = threadIdx.x; t < cnt; t += 2 * nt) {
+            {
+                const unsigned yy = __umulhi(t, m), xx = t - yy * w;
+                const int q = org + (int)yy * RS + (int)xx;
+                dst[q] = heat2d_update_int(hx, hy, rx, ry, src[q - 1], src[q + 1], src[q], src[q - RS], src[q + RS]);
+            }
+            const unsigned t2 = t + nt;
+            if (t2 < cnt) {
+                const unsigned yy = __umulhi(t2, m), xx = t2 - yy * w;
+                const int q = org + (int)yy * RS + (int)xx;
+                dst[q] = heat2d_update<O>(rx, ry, src[q - 1], src[q + 1], src[q], src[q - RS], src[q + RS]);
+            }
         }
     } else {
         const unsigned nb = min(max(__umulhi(NT, c_magic[w]), 1u), h);
@@ -347,7 +387,7 @@ __device__ void pyramid_part(const Frame<T> &f, const Swept2DArgs<T> &a, int W, 
     T *sxb = strip_block(sx, tile, 0, H, W), *syb = strip_block(sy, tile, 0, H, W);
     export_pyramid<NT>(f, F, 0, H, W, sxb, syb);
     for (int i = 1; i < H; ++i) {
-        compute_window<NT>(f, F + i, i + 1, W - i, i + 1, W - i, a.rx, a.ry);
+        compute_window<NT>(f, F + i, i + 1, W - i, i + 1, W - i, a.rx, a.ry, a.hrx, a.hry);
         __syncthreads();
         export_pyramid<NT>(f, F + i, i, H, W, sxb, syb);
     }
@@ -405,8 +445,8 @@ __global__ void __launch_bounds__(NT, (min_ctas2d<T, NT>())) k2d_bridges(Swept2D
         si = i + 1;
         if (si < H) stage.fetch(W - 2 * i, get, where);
         // the widening direction's window [H + 1 - i, H + i], the narrowing one's [i + 1, W - i]
-        if (xb) compute_window<NT>(f, base + i, H + 1 - i, H + i, i + 1, W - i, a.rx, a.ry);
-        else compute_window<NT>(f, base + i, i + 1, W - i, H + 1 - i, H + i, a.rx, a.ry);
+        if (xb) compute_window<NT>(f, base + i, H + 1 - i, H + i, i + 1, W - i, a.rx, a.ry, a.hrx, a.hry);
+        else compute_window<NT>(f, base + i, i + 1, W - i, H + 1 - i, H + i, a.rx, a.ry, a.hrx, a.hry);
         if (si < H) stage.put(f.s, W - 2 * i, get, where);
         __syncthreads();
         // export the edges along the widening direction's normal: an x-bridge its bottom and
@@ -484,7 +524,7 @@ __global__ void __launch_bounds__(NT, (min_ctas2d<T, NT>())) k2d_octa(Swept2DArg
             stage.fetch(2 * i, get, where);
             corner(si);
         }
-        compute_window<NT>(f, base + i, H + 1 - i, H + i, H + 1 - i, H + i, a.rx, a.ry);
+        compute_window<NT>(f, base + i, H + 1 - i, H + i, H + 1 - i, H + i, a.rx, a.ry, a.hrx, a.hry);
         if (si <= H) {
             stage.put(f.s, 2 * i, get, where);
             if (cpos >= 0) f.s[cpos] = cv;
@@ -639,6 +679,7 @@ int run_perstep2d(sw_handle2d *h, T *state, int64_t steps, cudaStream_t st, int6
     const int64_t nx = h->prob.nx, ny = h->prob.ny;
     const int periodic = h->prob.boundary == SW_PERIODIC;
     const T rx = (T)h->prob.rx, ry = (T)h->prob.ry;
+    const soft64::HeatR hx = soft64::make_heat_r(h->prob.rx), hy = soft64::make_heat_r(h->prob.ry);
     T *bufs[2] = {state, reinterpret_cast<T *>(h->plane)};
     const int cap = 152 * 16;
     // 16-byte row pieces need the state (the scratch plane is 256-byte aligned) and every
@@ -649,12 +690,14 @@ int run_perstep2d(sw_handle2d *h, T *state, int64_t steps, cudaStream_t st, int6
         T *out = bufs[(s + 1) & 1];
         trace2d_begin(h, launches, 3, st);
         if (vec)
-            k2d_step<T, 4, true><<<grid2d(nx / 4 * ny, cap), kThreads2D, 0, st>>>(in, out, nx, ny, rx, ry, periodic);
+            k2d_step<T, 4, true><<<grid2d(nx / 4 * ny, cap), kThreads2D, 0, st>>>(in, out, nx, ny, rx, ry, periodic, hx,
+                                                                                  hy);
         else if (nx % 4 == 0)
             k2d_step<T, 4, false><<<grid2d(nx / 4 * ny, cap), kThreads2D, 0, st>>>(in, out, nx, ny, rx, ry,
-                                                                                   periodic);
+                                                                                   periodic, hx, hy);
         else
-            k2d_step<T, 1, false><<<grid2d(nx * ny, cap), kThreads2D, 0, st>>>(in, out, nx, ny, rx, ry, periodic);
+            k2d_step<T, 1, false><<<grid2d(nx * ny, cap), kThreads2D, 0, st>>>(in, out, nx, ny, rx, ry, periodic, hx,
+                                                                               hy);
         trace2d_end(h, launches, st);
         ++launches;
     }
@@ -683,6 +726,8 @@ template <class T> int run2d(sw_handle2d *h, void *state_v, int64_t nsteps, cuda
             a.state = state;
             a.rx = (T)h->prob.rx;
             a.ry = (T)h->prob.ry;
+            a.hrx = soft64::make_heat_r(h->prob.rx);
+            a.hry = soft64::make_heat_r(h->prob.ry);
             a.brx = reinterpret_cast<T *>(h->brx);
             a.bry = reinterpret_cast<T *>(h->bry);
             const unsigned tiles = (unsigned)(h->Mx * h->My);

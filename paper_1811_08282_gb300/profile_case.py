@@ -34,7 +34,8 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=1 << 24)
     ap.add_argument("--steps", type=int, default=2048)
     ap.add_argument("--width", type=int, default=1024)
-    ap.add_argument("--r", type=float, default=0.3)
+    ap.add_argument("--r", type=float, default=None,
+                    help="heat: r (default 0.3); heat2d: rx = ry (default 0.2, stable: rx + ry <= 1/2)")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--threads", type=int, default=0, help="heat2d swept: threads per CTA (0: the default)")
     ap.add_argument("--bridge-threads", type=int, default=0, help="heat2d swept: threads per bridges CTA")
@@ -50,6 +51,8 @@ def main(argv=None):
     if a.scheme == "batch":
         return run_batch(a)
     heat = a.scheme == "heat"
+    if a.r is None:
+        a.r = 0.3
     bc = a.boundary or ("periodic" if heat else "transmissive")
     p = S.Problem(scheme=S.SW_HEAT if heat else S.SW_EULER, precision=PREC[a.precision],
                   boundary=S.SW_PERIODIC if bc == "periodic" else S.SW_TRANSMISSIVE,
@@ -114,6 +117,8 @@ def run_batch(a) -> int:
 def run2d(a) -> int:
     """The 2D heat case: 16 seeded separable modes, r = a.r in both directions."""
     import torch
+    if a.r is None:
+        a.r = 0.2
     p = S.Heat2D(precision=PREC[a.precision], method=S.SW_SWEPT if a.method == "swept" else S.SW_PERSTEP,
                  tile_width=a.width if a.method == "swept" else 0, nx=a.nx, ny=a.ny, rx=a.r, ry=a.r)
     x = I.heat2d_initial(I.heat2d_modes(a.nx, a.ny, 16, seed=1, kmax=16))

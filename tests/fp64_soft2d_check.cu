@@ -1,5 +1,5 @@
 // Host-only harness for tests/test_fp64_soft.py: the integer-pipe FP64 update of the 2D heat
-// kernels (soft64::heat2d_update in csrc/fp64_soft.cuh, compiled here as host code) against the
+// kernels (soft64::heat2d_update in csrc/fp64_soft2d.cuh, compiled here as host code) against the
 // host's own IEEE 754 binary64 arithmetic,
 //   fma(rx, fma(-2, u, a + b), fma(ry, fma(-2, u, d + e), u))
 // with std::fma and no contraction. Every case the integer path accepts must give the same bits.
@@ -12,7 +12,7 @@
 #include <random>
 #include <vector>
 
-#include "fp64_soft.cuh"
+#include "fp64_soft2d.cuh"
 
 using namespace sw;
 
