@@ -23,7 +23,9 @@
 #include "problem.h"
 #include "fold.h"
 #include "perstep.cuh"
-#include "schemes.cuh"
+#include "euler.cuh"
+#include "heat.cuh"
+#include "heat_policy.cuh"
 #include "swept_phase.cuh"
 
 using namespace sw;

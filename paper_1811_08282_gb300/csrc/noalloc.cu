@@ -22,7 +22,9 @@
 
 #include "../../include/swept.h"
 #include "problem.h"
-#include "schemes.cuh"
+#include "euler.cuh"
+#include "heat.cuh"
+#include "heat_policy.cuh"
 #include "swept_phase.cuh"
 
 using namespace sw;

@@ -11,7 +11,9 @@
 #include <type_traits>
 
 #include "fp64_soft.cuh"
-#include "schemes.cuh"
+#include "euler.cuh"
+#include "heat.cuh"
+#include "heat_policy.cuh"
 
 namespace sw {
 
