@@ -8,7 +8,7 @@ namespace sw {
 
 bool fold_supported(int precision, int W) {
     if (precision < SW_FP64 || precision > SW_FP32_COMP) return false;
-    return W == 128 || W == 256 || W == 512 || W == 1024;
+    return W == 64 || W == 128 || W == 256 || W == 512 || W == 1024;
 }
 
 // Measured on GB300 at N = 2^24 (diamond phases, 4-warp CTAs; multiples of 4 keep
@@ -48,6 +48,7 @@ static cudaError_t go(const FoldPhase &ph, const HeatParams &prm, int64_t warps,
 template <class C>
 static cudaError_t by_width(int W, const FoldPhase &ph, const HeatParams &prm, int64_t warps, cudaStream_t st) {
     switch (W) {
+    case 64: return go<2, C>(ph, prm, warps, st);
     case 128: return go<4, C>(ph, prm, warps, st);
     case 256: return go<8, C>(ph, prm, warps, st);
     case 512: return go<16, C>(ph, prm, warps, st);

@@ -10,7 +10,7 @@
 namespace sw {
 
 // True when k_heat_fold has an instantiation for this precision and base width
-// (W = 32 K, K in {4, 8, 16, 32}).
+// (W = 32 K, K in {2, 4, 8, 16, 32}).
 bool fold_supported(int precision, int W);
 
 // One phase of a periodic heat problem with M tiles (p: 0 Up Triangle, 1 seam

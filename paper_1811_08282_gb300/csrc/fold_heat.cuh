@@ -158,10 +158,12 @@ __global__ void __launch_bounds__(128) k_heat_fold(FoldArgs<typename C::T> a, He
     const bool up = a.p == 0;
     const int imax = up ? a.upper : (a.lower > a.upper ? a.lower : a.upper);
 
-    // integer-pipe slots (up to K = 8: beyond, the extra registers spill): r
-    // unpacked once (an r outside its range fails every soft update, which then
-    // runs on the FP64 pipe)
-    constexpr int SOFT = K <= 8 ? C::SOFT_EVERY : 0;
+    // integer-pipe slots for K = 4 .. 8 (beyond, the extra registers spill; at K = 2, W = 64,
+    // the grids that choose it are small and latency-bound, where the integer path's long
+    // dependent chain costs more than the FP64 pipe it frees: 1.17 against 0.80 ms for
+    // N = 16384 x 1000 steps): r unpacked once (an r outside its range fails every soft
+    // update, which then runs on the FP64 pipe)
+    constexpr int SOFT = (K >= 4 && K <= 8) ? C::SOFT_EVERY : 0;
     soft64::HeatR hr{};
     if constexpr (SOFT > 0) hr = soft64::make_heat_r(prm.r);
     V v[K];

@@ -78,6 +78,10 @@ def test_fp32_variants_swept_equals_perstep(prec, tol, n, W, steps, bc, r):
 @pytest.mark.parametrize("n,W,steps", [
     (256, 128, 300),       # two diamonds per phase: one per warp
     (1024, 128, 1000),
+    (192, 64, 77),         # W = 64 (two cells per lane): three tiles, an odd number of diamonds
+    (4096, 64, 31),        # shorter than one Up Triangle
+    (4096, 64, 96),        # a multiple of W/2: complete Down Triangle
+    (16384, 64, 1000),     # the small-grid workload's shape
     (4096, 256, 777),      # ragged last phases run on the generic kernel
     (1 << 16, 512, 1500),
     (1 << 15, 1024, 2100),
