@@ -320,8 +320,10 @@ SW_API int sw_batch_debug(sw_batch *b, int64_t wait_budget_cycles, int32_t drop_
 SW_API void sw_batch_destroy(sw_batch *b);
 
 /* Tile-width autotuner (Section 6 advises tuning the block size on a
- * few short runs): times `probe_steps` steps of a uniform state
- * of the problem for each W in {32, ..., 1024} that divides n (with n >= 2W),
+ * few short runs): times `probe_steps` steps of a probe state (heat: 1.5 +
+ * a smooth sine, one sign, as the data-dependent FP64 integer-pipe path expects of
+ * smooth fields; Euler: uniform, at rest) for each W in {32, ..., 1024} that divides
+ * n (with n >= 2W),
  * using the problem's own flags (SW_FLAG_GENERIC tunes the generic kernel that
  * batches use), and writes the fastest to inout->tile_width. For an Euler
  * problem with neither SW_FLAG_LENGTHENED nor SW_FLAG_FLATTENED it times both

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -543,15 +544,22 @@ int sw_autotune(sw_problem *inout, int64_t probe_steps, void *stream) {
     void *state = nullptr;
     cudaError_t e = cudaMalloc(&state, (size_t)bytes);
     if (e != cudaSuccess) return cuda_status_b(e);
-    // a valid uniform state: heat 0, Euler (rho, m, E) = (1, 0, 2.5)
+    // the probe state (the kernels' cost depends on the data): heat 1.5 + sin of 8 waves, smooth
+    // and of one sign, so that the FP64 integer-pipe path takes the cells it takes on smooth
+    // fields (a zero state would send every one of them to the FP64 pipe); Euler a uniform state
+    // at rest, (rho, m, E) = (1, 0, 2.5), stable at any dt/dx a caller may give
     {
         const int64_t nv = p.scheme == SW_HEAT ? 1 : 3;
         std::vector<double> h((size_t)(nv * p.n), 0.0);
-        if (p.scheme == SW_EULER)
-            for (int64_t i = 0; i < p.n; ++i) {
+        const double k = 2.0 * 3.14159265358979323846 * 8.0 / (double)p.n;
+        for (int64_t i = 0; i < p.n; ++i) {
+            if (p.scheme == SW_HEAT) {
+                h[(size_t)i] = 1.5 + std::sin(k * (double)i);
+            } else {
                 h[(size_t)i] = 1.0;
                 h[(size_t)(2 * p.n + i)] = 2.5;
             }
+        }
         double *d64 = nullptr;
         e = cudaMalloc(&d64, sizeof(double) * h.size());
         if (e != cudaSuccess) {
