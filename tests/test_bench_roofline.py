@@ -52,3 +52,29 @@ def test_two_pipe_ceiling_takes_the_busier_pipe():
     assert bench.ALU_LANE_INST_PER_S / a < bench.FP64_INST_PER_S / f
     ceiling = min(bench.FP64_INST_PER_S / f, bench.ALU_LANE_INST_PER_S / a)
     assert 390e9 < ceiling < 398e9
+
+
+def test_committed_counts_are_current_for_every_recorded_kernel():
+    # every kernel with recorded ncu figures must still have the sources they were taken from,
+    # or the bench line would drop its traffic and instruction counts (null)
+    path = os.path.join(bench.ROOT, "profiles", "traffic.txt")
+    shas = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#") and ".source_sha=" in line:
+            k, v = line.split(".source_sha=")
+            shas[k] = v
+    assert {"k_heat_fold", "k2d"} <= set(shas)
+    for kernel, sha in shas.items():
+        assert bench.kernel_source_sha(kernel) == sha, kernel
+
+
+def test_2d_ceiling_is_the_busier_pipe_for_the_recorded_mix():
+    fp64_rate, alu_rate = 528.8e9, 16.05e12
+    ceil, f, a = bench.pipe_ceiling2d("k2d.phase_fp64.w64", fp64_rate, alu_rate)
+    assert ceil == min(fp64_rate / f, alu_rate / a)
+    assert 2.5 < f < 4.0 and 60 < a < 130  # about half the cells on each pipe
+    assert 140e9 < ceil < 190e9
+    step, f2, a2 = bench.pipe_ceiling2d("k2d.step_fp64", fp64_rate, alu_rate)
+    assert step == min(fp64_rate / f2, alu_rate / a2)
+    assert bench.pipe_ceiling2d("k2d.phase_fp64.w32", fp64_rate, alu_rate) == (None, None, None)
